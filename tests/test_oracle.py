@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix:
+hand-worked fixtures, brute force on tiny inputs, closed forms, invariants
+and synthetic-haze recovery. CPU only."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import hazegen
+from oracle import hazedefy_oracle as O
+from tests.golden_io import read_dark_channel_fixture
+
+
+def loop_patch_min(x, patch):
+    """Independent per-pixel loop: min over the clipped window."""
+    r = patch // 2
+    H, W = x.shape
+    out = np.empty_like(x)
+    for y in range(H):
+        for xx in range(W):
+            out[y, xx] = x[max(0, y - r):y + r + 1, max(0, xx - r):xx + r + 1].min()
+    return out
+
+
+# ------------------------------------------------------------- Eq. 2 ----
+
+def test_dark_channel_hand_fixture():
+    I, m, D3, _ = read_dark_channel_fixture()
+    assert I.shape == (4, 5, 3)
+    np.testing.assert_array_equal(O.channel_min(I), m)
+    np.testing.assert_array_equal(O.dark_channel(I, 3), D3)
+    np.testing.assert_array_equal(O.dark_channel(I, 1), m)
+
+
+@pytest.mark.parametrize("H,W,patch", [(1, 1, 15), (7, 3, 3), (5, 17, 5), (16, 9, 15),
+                                       (13, 13, 7), (2, 30, 31), (9, 4, 1)])
+def test_patch_min_vs_loop(H, W, patch):
+    g = np.random.default_rng(H * 100 + W + patch)
+    x = g.integers(0, 256, size=(H, W)).astype(np.float64)
+    np.testing.assert_array_equal(O.patch_min(x, patch), loop_patch_min(x, patch))
+
+
+def test_dark_channel_constant_image():
+    I = np.empty((20, 33, 3), np.uint8)
+    I[:] = (200, 37, 90)
+    for patch in (1, 3, 15):
+        assert np.all(O.dark_channel(I, patch) == 37)
+
+
+def test_dark_channel_huge_patch_is_global_min():
+    I = hazegen.random_u8_image(11, 7, seed=3)
+    D = O.dark_channel(I, 2 * 11 + 1)
+    assert np.all(D == I.min())
+
+
+def test_dark_channel_patch1_is_channel_min():
+    I = hazegen.random_u8_image(19, 6, seed=4)
+    np.testing.assert_array_equal(O.dark_channel(I, 1), I.min(axis=2))
+
+
+def test_patch_min_rejects_even():
+    with pytest.raises(ValueError):
+        O.patch_min(np.zeros((3, 3)), 4)
+
+
+# ------------------------------------------------------------- Eq. 3 ----
+
+def test_selection_hand_fixture():
+    I, _, _, selects = read_dark_channel_fixture()
+    for s in selects:
+        D = O.dark_channel(I, s["patch"])
+        sel = O.select_top(D, s["K"])
+        assert sel["T"] == s["T"]
+        assert sel["n_above"] == s["n_above"]
+        assert sel["cut_index"] == s["cut_index"]
+        assert list(sel["idx"]) == s["idx"]
+        S = I.reshape(-1, 3)[sel["idx"]].astype(np.int64).sum(axis=0)
+        assert list(S) == s["S"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_select_top_vs_python_sort(seed):
+    g = np.random.default_rng(seed)
+    H, W = int(g.integers(1, 9)), int(g.integers(1, 9))
+    D = g.integers(0, 4, size=(H, W)).astype(np.uint8)  # many ties
+    N = H * W
+    for K in range(1, N + 1):
+        keyed = sorted(range(N), key=lambda i: (-int(D.reshape(-1)[i]), i))
+        want = sorted(keyed[:K])
+        sel = O.select_top(D, K)
+        assert list(sel["idx"]) == want
+        flat = D.reshape(-1)
+        T = int(flat[keyed[K - 1]])
+        assert sel["T"] == T
+        assert sel["n_above"] == sum(1 for v in flat if v > T)
+        ties = [i for i in keyed[:K] if flat[i] == T]
+        assert sel["cut_index"] == max(ties)
+
+
+def test_select_k1_is_first_argmax_and_kN_is_all():
+    D = np.array([[3, 7, 7], [7, 1, 0]], np.uint8)
+    s1 = O.select_top(D, 1)
+    assert list(s1["idx"]) == [1] and s1["T"] == 7
+    sN = O.select_top(D, 6)
+    assert list(sN["idx"]) == list(range(6)) and sN["T"] == 0
+
+
+@pytest.mark.parametrize("W,H,K", [(640, 480, 307), (854, 480, 409), (1280, 720, 921),
+                                   (1920, 1080, 2073), (3840, 2160, 8294), (1, 1, 1), (10, 10, 1)])
+def test_num_top(W, H, K):
+    assert O.num_top(W * H, 0.001) == K
+
+
+def test_num_top_caps():
+    assert O.num_top(50, 1.0) == 50
+    assert O.num_top(50, 5.0) == 50
+    assert O.num_top(50, 0.0) == 1
+    assert O.num_top(0, 0.1) == 0
+
+
+def test_airlight_recovery_from_opaque_sky():
+    """A region with t = 0 shows I = A* exactly (Eq. 1); if it holds >= K
+    pixels and the rest of the scene is darker, Eq. 3 with alpha = 1 returns
+    A* up to the 0.5/255 quantisation of the frame."""
+    W, H = 64, 48
+    g = np.random.default_rng(7)
+    A_star = np.array([0.86, 0.9, 0.93])
+    J = g.uniform(0, 1, size=(H, W, 3))
+    J[:, :, int(g.integers(0, 3))] *= 0.05
+    t = np.full((H, W), 0.6)
+    t[:12, :] = 0.0  # opaque sky: 12 * 64 = 768 px
+    I = J * t[:, :, None] + A_star * (1 - t[:, :, None])
+    I8 = np.clip(np.rint(255 * I), 0, 255).astype(np.uint8)
+    D = O.dark_channel(I8, 15)
+    al = O.airlight(I8, D, 0.1, 1.0)  # K = 307 < 768
+    assert al["K"] == 307
+    assert np.all(np.abs(al["A_hat"] - A_star) <= 0.5 / 255 + 1e-12)
+    al8 = O.airlight(I8, D, 0.1, 0.8)
+    np.testing.assert_allclose(al8["A_hat"], 0.8 * al["A_hat"], rtol=1e-15)
+
+
+def test_ema_closed_form():
+    a, b, lam = np.array([0.9, 0.8, 0.7]), np.array([0.5, 0.6, 0.65]), 0.9
+    seq = [a] + [b] * 20
+    out = O.ema_airlight(seq, lam)
+    for f in range(21):
+        want = b + lam ** f * (a - b)
+        np.testing.assert_allclose(out[f], want, rtol=0, atol=1e-14)
+    const = O.ema_airlight([a] * 5, lam)
+    np.testing.assert_allclose(const, np.array([a] * 5), atol=1e-15)
+    np.testing.assert_array_equal(O.ema_airlight([a, b], 0.0)[1], b)
+
+
+# ----------------------------------------------------------- Eq. 4-5 ----
+
+def _blocky_scene(W, H, seed, block=24):
+    """J with a zero blue channel (dark-channel prior exact for every patch),
+    t constant on block x block squares, known A."""
+    g = np.random.default_rng(seed)
+    J = g.uniform(0.2, 1.0, size=(H, W, 3))
+    J[:, :, 2] = 0.0
+    tb = g.uniform(0.3, 0.95, size=((H + block - 1) // block, (W + block - 1) // block))
+    t = np.kron(tb, np.ones((block, block)))[:H, :W]
+    A = np.array([0.88, 0.9, 0.92])
+    I = J * t[:, :, None] + A * (1 - t[:, :, None])
+    return J, t, A, np.clip(np.rint(255 * I), 0, 255).astype(np.uint8)
+
+
+def test_transmission_recovers_t_closed_form():
+    """With min_c J^c/A^c = 0 on a patch and t constant on it,
+    min_Omega min_c I^c/A^c = 1 - t*, so omega = 1 returns t* up to the
+    quantisation bound 0.5/(255 min A) (Eq. 1 inverted by the patch form)."""
+    W, H, block, patch = 96, 72, 24, 15
+    J, t_star, A, I8 = _blocky_scene(W, H, 1, block)
+    t = O.transmission_dcp(I8, A, 1.0, 0.0, patch)
+    r = patch // 2
+    mask = np.zeros((H, W), bool)
+    for by in range(0, H, block):
+        for bx in range(0, W, block):
+            mask[by + r:by + block - r, bx + r:bx + block - r] = True
+    err = np.abs(t - t_star)[mask]
+    assert err.max() <= 0.5 / (255 * A.min()) + 1e-12
+
+
+def test_transmission_bounds_and_omega0():
+    I = hazegen.make_frame(40, 30, seed=5)
+    A = [0.8, 0.85, 0.9]
+    t = O.transmission_dcp(I, A, 0.95, 0.1, 15)
+    assert t.min() >= 0.1 and t.max() <= 1.0
+    assert np.all(O.transmission_dcp(I, A, 0.0, 0.1, 15) == 1.0)
+    tf = O.transmission_fast(I, A, 0.5, 0.05)
+    assert tf.min() >= 0.05 and tf.max() <= 1.0
+    assert np.all(O.transmission_fast(I, A, 0.0, 0.05) == 1.0)
+
+
+def test_transmission_fast_pointwise_closed_form():
+    """Eq. 4 on single pixels: m = min channel, t = 1 - omega m/(255 maxA)."""
+    I = np.array([[[255, 128, 64], [10, 20, 30]]], np.uint8)
+    A = [0.5, 0.8, 0.4]
+    t = O.transmission_fast(I, A, 0.5, 0.05)
+    assert t[0, 0] == pytest.approx(1 - 0.5 * (64 / 255) / 0.8, abs=1e-15)
+    assert t[0, 1] == pytest.approx(1 - 0.5 * (10 / 255) / 0.8, abs=1e-15)
+    I2 = np.array([[[255, 255, 255]]], np.uint8)
+    assert O.transmission_fast(I2, [0.2, 0.2, 0.2], 0.5, 0.05)[0, 0] == 0.05
+
+
+def test_transmission_dcp_patch1_matches_per_pixel_ratio():
+    I = hazegen.random_u8_image(9, 8, seed=11)
+    A = np.array([0.7, 0.9, 0.8])
+    t = O.transmission_dcp(I, A, 0.9, 0.0, 1)
+    ratio = np.array([[min(I[y, x, c] / 255 / A[c] for c in range(3)) for x in range(9)] for y in range(8)])
+    np.testing.assert_allclose(t, 1 - 0.9 * ratio, atol=1e-15)
+
+
+# ------------------------------------------------------------- Eq. 6 ----
+
+@pytest.mark.parametrize("H,W,r", [(9, 13, 2), (5, 4, 3), (12, 12, 5), (1, 7, 1)])
+def test_box_mean_sat_vs_brute(H, W, r):
+    x = np.random.default_rng(H + W + r).normal(size=(H, W))
+    np.testing.assert_allclose(O.box_mean(x, r), O.box_mean_brute(x, r), atol=1e-13)
+
+
+def test_guided_constant_p_is_identity():
+    I = hazegen.make_frame(40, 32, seed=2)
+    G = O.gray(I)
+    p = np.full(G.shape, 0.37)
+    np.testing.assert_allclose(O.guided_filter(G, p, 6, 1e-3), p, atol=1e-12)
+
+
+def test_guided_linear_p_eps0_is_identity():
+    g = np.random.default_rng(3)
+    G = g.uniform(0, 1, size=(30, 26))  # no flat windows
+    p = 0.7 * G + 0.2
+    np.testing.assert_allclose(O.guided_filter(G, p, 4, 0.0), p, atol=1e-9)
+
+
+def test_guided_large_eps_is_double_box():
+    g = np.random.default_rng(4)
+    G = g.uniform(0, 1, size=(25, 31))
+    p = g.uniform(0.1, 1, size=G.shape)
+    q = O.guided_filter(G, p, 3, 1e12)
+    want = O.box_mean(O.box_mean(p, 3), 3)
+    np.testing.assert_allclose(q, want, atol=1e-9)
+
+
+def test_guided_with_brute_mean_matches_sat():
+    g = np.random.default_rng(5)
+    G = g.uniform(0, 1, size=(14, 11))
+    p = g.uniform(0.1, 1, size=G.shape)
+    a = O.guided_filter(G, p, 3, 1e-3)
+    b = O.guided_filter(G, p, 3, 1e-3, mean=O.box_mean_brute)
+    np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+def test_gray_weights_pin():
+    I = np.array([[[255, 0, 0], [0, 255, 0], [0, 0, 255], [255, 255, 255]]], np.uint8)
+    np.testing.assert_allclose(O.gray(I)[0], [0.299, 0.587, 0.114, 1.0], atol=1e-15)
+
+
+# ----------------------------------------------------------- Eq. 7-8 ----
+
+def test_recover_I_equals_A_gives_A():
+    g = np.random.default_rng(6)
+    I = np.empty((10, 12, 3), np.uint8)
+    I[:] = (200, 180, 230)
+    A = I[0, 0].astype(np.float64) / 255
+    t = g.uniform(0.05, 1, size=(10, 12))
+    np.testing.assert_allclose(O.recover(I, t, A), np.broadcast_to(A, I.shape), atol=1e-15)
+
+
+def test_recover_inverts_scattering_model():
+    """Eq. 7 is the inverse of Eq. 1 for a known t and A."""
+    g = np.random.default_rng(8)
+    J = g.uniform(0, 1, size=(6, 7, 3))
+    t = g.uniform(0.2, 1, size=(6, 7))
+    A = np.array([0.8, 0.85, 0.9])
+    I = J * t[:, :, None] + A * (1 - t[:, :, None])
+    # feed the exact float I through the u8 path at scale: use a u8 frame
+    I8 = np.clip(np.rint(255 * I), 0, 255).astype(np.uint8)
+    Jr = O.recover(I8, t, A)
+    bound = 0.5 / 255 / t.min() + 1e-12
+    assert np.abs(Jr - J).max() <= bound
+
+
+def test_gamma_closed_forms():
+    J = np.linspace(0, 1, 11).reshape(1, 11, 1).repeat(3, axis=2)
+    np.testing.assert_array_equal(O.gamma_correct(J, 1.0), J)
+    np.testing.assert_allclose(O.gamma_correct(J, 2.0), np.sqrt(J), atol=1e-15)
+    # Eq. 8 on a 255 scale equals the normalised form
+    J255 = 255 * J
+    np.testing.assert_allclose(255 * (J255 / 255) ** (1 / 1.2), 255 * O.gamma_correct(J, 1.2), atol=1e-12)
+
+
+def test_quantize_half_even():
+    x = np.array([0.5, 1.5, 2.5, 254.5, 0.49, 255.0]) / 255
+    np.testing.assert_array_equal(O.quantize(x), [0, 2, 2, 254, 0, 255])
+
+
+def test_gray_world_invariants():
+    g = np.random.default_rng(9)
+    v = g.uniform(0.1, 0.6, size=(8, 9))
+    grey = np.repeat(v[:, :, None], 3, axis=2)
+    out, gains, _ = O.gray_world(grey)
+    np.testing.assert_allclose(gains, 1.0, atol=1e-15)
+    np.testing.assert_allclose(out, grey, atol=1e-15)
+    col = g.uniform(0.05, 0.5, size=(8, 9, 3)) * np.array([1.0, 0.7, 0.4])
+    out, gains, mu = O.gray_world(col)
+    m = out.reshape(-1, 3).mean(axis=0)  # no clipping at these values
+    np.testing.assert_allclose(m, m.mean(), rtol=1e-12)
+    zero = col.copy()
+    zero[:, :, 1] = 0
+    _, gz, _ = O.gray_world(zero)
+    assert gz[1] == 1.0
+
+
+# ------------------------------------------------------------ pipeline ----
+
+def test_pipeline_identity_when_omega0_gamma1():
+    I = hazegen.make_frame(48, 40, seed=12)
+    prm = O.OracleParams(omega=0.0, gamma=1.0, color_balance=False)
+    res = O.dehaze_frame(I, prm)
+    np.testing.assert_array_equal(res.out, I)
+
+
+def test_pipeline_recovers_scene_with_known_airlight():
+    """Synthetic haze with an exact dark prior and blockwise-constant t:
+    with A forced to A*, omega = 1 and gamma = 1 the output equals the
+    clear scene away from block edges, within the quantisation slop."""
+    W, H, block = 96, 72, 24
+    J, t_star, A, I8 = _blocky_scene(W, H, 2, block)
+    prm = O.OracleParams(omega=1.0, t0=0.01, gamma=1.0, airlight_override=tuple(A))
+    res = O.dehaze_frame(I8, prm)
+    r = prm.patch // 2
+    mask = np.zeros((H, W), bool)
+    for by in range(0, H, block):
+        for bx in range(0, W, block):
+            mask[by + r:by + block - r, bx + r:bx + block - r] = True
+    err = np.abs(res.out.astype(float) / 255 - J)[mask]
+    # dt <= 0.5/(255 minA); J error <= (|I-A| dt + 0.5/255) / t + 0.5/255
+    bound = (1.0 * 0.5 / (255 * A.min()) + 0.5 / 255) / t_star.min() + 0.5 / 255
+    assert err.max() <= bound
+
+
+def test_pipeline_sequence_ema_and_balance_shapes():
+    frames = [hazegen.make_frame(32, 24, seed=s, beta=1.0) for s in (1, 2, 3)]
+    prm = O.OracleParams(airlight_ema=0.9, color_balance=True)
+    res = O.dehaze_sequence(frames, prm)
+    A = O.ema_airlight([r.A_hat for r in res], 0.9)
+    for f in range(3):
+        np.testing.assert_allclose(res[f].A, A[f], atol=1e-15)
+        assert res[f].out.shape == (24, 32, 3) and res[f].out.dtype == np.uint8
+        assert res[f].t.min() >= prm.t0 - 1e-15
+
+
+def test_image_mode_t_within_bounds():
+    I = hazegen.make_frame(50, 40, seed=13, beta=1.2)
+    prm = O.OracleParams(gf_radius=6)
+    res = O.dehaze_image(I, prm)
+    assert res.t.min() >= prm.t0 and res.t.max() <= 1.0
+    assert res.t_coarse is not None
+
+
+def test_params_f32_rounding():
+    p = O.OracleParams().f32()
+    assert p.omega == float(np.float32(0.95))
+    assert p.alpha == float(np.float32(0.8))
