@@ -1,0 +1,288 @@
+/*
+ * hazedefy.h - C interface of the GB300 (sm_103a) Hazedefy dehazing library.
+ *
+ * The library restores a hazy RGB frame I with the atmospheric scattering
+ * model I = J t + A (1 - t) (Section III, Eq. 1) by the per-frame algorithm of
+ * Section V: per-pixel channel minimum and patch minimum filter (dark channel,
+ * Section IV-A, Eq. 2), airlight from the average of the top-K dark-channel
+ * pixels (Section IV-B, Eq. 3), lower-bounded transmission (Section IV-C,
+ * Eq. 4-5), guided-filter refinement in image mode (Section IV-D, Eq. 6),
+ * radiance reconstruction (Section IV-E, Eq. 7), gamma correction (Eq. 8) and
+ * an optional colour balance (Section IV-E, after Eq. 8).
+ *
+ * Conventions shared by every call:
+ *  - Frames are 8-bit RGB, channel order r, g, b, interleaved (3 bytes per
+ *    pixel), rows of 3*W bytes separated by a row pitch in bytes >= 3*W.
+ *    Any pitch and any pointer alignment are accepted; a pitch that is a
+ *    multiple of 16 bytes with a 16-byte aligned base is the fast layout.
+ *    The library may read whole aligned 16-byte words that contain at least
+ *    one byte of a frame (never a byte on a page that holds none).
+ *  - Buffer pointers are device pointers unless HZ_IO_HOST is given. The
+ *    caller owns every buffer it passes; the library never frees them. The
+ *    context owns all scratch memory and per-stream state.
+ *  - Work is enqueued on the CUDA stream passed as void* (a cudaStream_t;
+ *    NULL = legacy default stream) and is asynchronous with respect to the
+ *    host, unless an hz_frame_info pointer is passed, which makes the call
+ *    wait for that stream before returning.
+ *  - Every call returns an hz_status and never aborts. HZ_EINVAL marks bad
+ *    arguments (nothing is enqueued), HZ_ECUDA a CUDA runtime failure; the
+ *    detail is in hz_last_error(ctx). The hz_dehaze_* / stage calls on one
+ *    context must not be made concurrently from several host threads;
+ *    hz_submit / hz_poll are thread-safe.
+ *  - Sizes: 1 <= W, H <= 16384 and W*H <= 2^28.
+ */
+#ifndef HAZEDEFY_H
+#define HAZEDEFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HZ_ABI_VERSION 1
+
+typedef enum hz_status {
+  HZ_OK = 0,
+  HZ_EAGAIN = 1,            /* hz_poll: ticket not finished yet */
+  HZ_EINVAL = -1,           /* invalid argument */
+  HZ_ENOMEM = -2,           /* device or host allocation failed */
+  HZ_EBUSY = -3,            /* stream admission refused (memory budget) */
+  HZ_ETIMEDOUT = -4,        /* hz_poll: timeout expired */
+  HZ_ECUDA = -5,            /* CUDA runtime error */
+  HZ_EDEVICE_TIMEOUT = -6,  /* a bounded device-side wait gave up */
+  HZ_ESTATE = -7            /* call not valid in the current state */
+} hz_status;
+
+/* Transmission form (Section IV-C).
+ * HZ_T_DCP : t = max(1 - omega * min_{y in patch(x)} min_c I^c(y)/A^c, t0)
+ *            (dark channel of I/A; the default).
+ * HZ_T_FAST: t = max(1 - omega * min_c I^c(x) / max_c A^c, t0)
+ *            (Eq. 4 with the Eq. 5 clamp, per pixel). */
+enum { HZ_T_DCP = 0, HZ_T_FAST = 1 };
+
+/* Storage precision of the image-mode planes (transmission and guided-filter
+ * a/b planes); arithmetic is FP32 in both. */
+enum { HZ_PREC_FP32 = 0, HZ_PREC_FP16 = 1 };
+
+enum { HZ_MAX_PATCH = 31, HZ_MAX_GF_RADIUS = 255, HZ_MAX_DIM = 16384 };
+
+/* flags */
+#define HZ_IO_HOST 0x1u  /* in/out are host memory; the library stages copies */
+#define HZ_GUIDED 0x2u   /* hz_open_stream: refine t with the guided filter */
+
+/* Parameters. Intensities are normalised to [0, 1] (I_n = I / 255); the
+ * airlight A is in the same units. Set struct_size = sizeof(hz_params). */
+typedef struct hz_params {
+  uint32_t struct_size;
+  int32_t patch;          /* odd, 1..HZ_MAX_PATCH; Section IV-A uses 15 */
+  float omega;            /* haze retention weight, [0, 1]; Eq. 4 */
+  float t0;               /* lower bound t_min, [0, 1); Eq. 5 */
+  float top_fraction;     /* K = max(1, floor(top_fraction*N)) capped at N;
+                             Section IV-B; (0, 1] */
+  float alpha;            /* airlight scale, Eq. 3 (0.8); (0, 4] */
+  float gamma;            /* Eq. 8; > 0 (the paper gives no value) */
+  int32_t t_mode;         /* HZ_T_DCP or HZ_T_FAST */
+  int32_t color_balance;  /* 0/1: gray-world gains after gamma */
+  float airlight_ema;     /* lambda in [0, 1): A_f = lambda A_{f-1} +
+                             (1 - lambda) Ahat_f across frames of a stream */
+  int32_t gf_radius;      /* guided filter radius r, 1..HZ_MAX_GF_RADIUS */
+  float gf_eps;           /* guided filter regulariser, >= 0 */
+  int32_t precision;      /* HZ_PREC_FP32 or HZ_PREC_FP16 */
+  int32_t use_airlight_override; /* 0/1: use airlight_override as A */
+  float airlight_override[3];    /* each in (0, 1] when used */
+} hz_params;
+
+/* Per-frame results. S, K, T, n_above and cut_index define the selected
+ * pixel set exactly: every pixel with D > T plus the pixels with D == T
+ * whose raster index y*W + x is <= cut_index. */
+typedef struct hz_frame_info {
+  float A[3];          /* airlight used for this frame (after smoothing) */
+  float A_hat[3];      /* this frame's own estimate (Eq. 3) */
+  int64_t K;           /* number of selected pixels */
+  int64_t n_above;     /* selected pixels with D > T */
+  int64_t cut_index;   /* raster index of the last selected tie (D == T) */
+  int64_t S[3];        /* integer sums of the selected pixels' r, g, b */
+  int32_t T;           /* dark-channel level of the K-th pixel */
+  int32_t status;      /* hz_status of this frame */
+  float gains[3];      /* colour-balance gains (1 when balance is off) */
+  float mean_jg[3];    /* channel means of J_gamma (0 when balance is off) */
+} hz_frame_info;
+
+/* One frame of a mixed-size batch (hz_dehaze_batch). */
+typedef struct hz_frame_desc {
+  const uint8_t* in;
+  size_t in_pitch;
+  uint8_t* out;
+  size_t out_pitch;
+  int32_t W;
+  int32_t H;
+  int32_t stream_id;  /* -1: stateless; else EMA state of an open stream */
+  uint32_t flags;     /* HZ_GUIDED: image mode for this frame */
+} hz_frame_desc;
+
+typedef struct hz_ctx hz_ctx;
+
+/* ------------------------------------------------------------ context -- */
+
+/* Fill *p with the defaults: patch 15, omega 0.95, t0 0.1, top_fraction
+ * 0.001, alpha 0.8, gamma 1.2, HZ_T_DCP, balance off, no smoothing,
+ * gf_radius 60, gf_eps 1e-3, FP32, no override. */
+void hz_params_default(hz_params* p);
+
+/* HZ_OK if every field is in range, else HZ_EINVAL. */
+hz_status hz_params_validate(const hz_params* p);
+
+/* Create a context on CUDA device `device`. mem_budget_bytes bounds the
+ * device memory the context may hold (0 = no bound besides free memory).
+ * On success *out owns the context; release it with hz_destroy. */
+hz_status hz_create(const hz_params* p, int device, size_t mem_budget_bytes, hz_ctx** out);
+
+/* Synchronise the context's work and free everything it owns. NULL is ok. */
+hz_status hz_destroy(hz_ctx* ctx);
+
+hz_status hz_get_params(const hz_ctx* ctx, hz_params* out);
+hz_status hz_set_params(hz_ctx* ctx, const hz_params* p);
+
+const char* hz_status_str(hz_status s);
+/* Detail of the last failing call on this context; owned by the context. */
+const char* hz_last_error(const hz_ctx* ctx);
+
+/* --------------------------------------------------------- video mode -- */
+
+/* Dehaze one frame (video mode: no guided filter; Section V algorithm).
+ * stream_id: -1 = stateless, else the airlight smoothing state of a stream
+ * opened with hz_open_stream. */
+hz_status hz_dehaze_frame(hz_ctx* ctx, int32_t stream_id, const uint8_t* in, int32_t W,
+                          int32_t H, size_t in_pitch, uint8_t* out, size_t out_pitch,
+                          void* cuda_stream, hz_frame_info* info);
+
+/* Dehaze n_frames frames of one size, frame f at in + f*in_frame_stride,
+ * in order, with the airlight of each frame smoothed with the previous one's
+ * when airlight_ema > 0 (the chain starts from the stream's state, or from
+ * frame 0's own estimate when stream_id = -1). flags: HZ_IO_HOST = in/out
+ * are host memory (pinned for overlap) and the library pipelines the copies.
+ * infos: NULL or n_frames records. */
+hz_status hz_dehaze_video(hz_ctx* ctx, int32_t stream_id, const uint8_t* in, int32_t n_frames,
+                          int32_t W, int32_t H, size_t in_pitch, size_t in_frame_stride,
+                          uint8_t* out, size_t out_pitch, size_t out_frame_stride,
+                          uint32_t flags, void* cuda_stream, hz_frame_info* infos);
+
+/* Dehaze n independent frames of any sizes in one batched launch.
+ * infos: NULL or n records. */
+hz_status hz_dehaze_batch(hz_ctx* ctx, const hz_frame_desc* frames, int32_t n,
+                          void* cuda_stream, hz_frame_info* infos);
+
+/* --------------------------------------------------------- image mode -- */
+
+/* Image mode (Section IV-D, Fig. 2): the video path plus the guided-filter
+ * refinement of t (guide = BT.601 grey of I_n, radius gf_radius, gf_eps),
+ * with the refined t clamped to [t0, 1]. Plane precision: params.precision. */
+hz_status hz_dehaze_image(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                          uint8_t* out, size_t out_pitch, void* cuda_stream, hz_frame_info* info);
+
+/* --------------------------------------------------------- stage calls -- */
+/* Single steps of the path, used to check each against a reference. */
+
+/* D(x) = min_{y in patch(x)} min_c I^c(y) (Eq. 2), window clipped to the
+ * image; D is uint8, H rows of W bytes at D_pitch. */
+hz_status hz_dark_channel(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                          uint8_t* D, size_t D_pitch, void* cuda_stream);
+
+/* Top-K selection and A_hat (Eq. 3); fills info (A = A_hat, no smoothing).
+ * Waits for the stream. */
+hz_status hz_estimate_airlight(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H,
+                               size_t in_pitch, void* cuda_stream, hz_frame_info* info);
+
+/* Transmission for a given airlight A[3] (host array, normalised), in the
+ * params' t_mode (Eq. 4-5 / dark channel of I/A). t: float32, H rows of W
+ * values at t_pitch bytes. */
+hz_status hz_transmission(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                          const float* A, float* t, size_t t_pitch, void* cuda_stream);
+
+/* q = GuidedFilter(p, I_gray, gf_radius, gf_eps) (Eq. 6, He et al. 2013 box
+ * form), guide = BT.601 grey of the RGB frame `in`. p and q: float32 planes
+ * (H rows of W values at their pitches in bytes). No clamp. */
+hz_status hz_guided_filter(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                           const float* p, size_t p_pitch, float* q, size_t q_pitch,
+                           void* cuda_stream);
+
+/* Reconstruction for a given t plane and A[3]: J = (I_n - A)/t + A (Eq. 7),
+ * clip to [0, 1], J^(1/gamma) (Eq. 8), colour balance if enabled, rint(255 x).
+ * info (optional) receives gains and means. */
+hz_status hz_recover(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                     const float* t, size_t t_pitch, const float* A, uint8_t* out,
+                     size_t out_pitch, void* cuda_stream, hz_frame_info* info);
+
+/* ------------------------------------------------------------ serving -- */
+/* Continuous batching: frames submitted from many streams are gathered each
+ * scheduler tick into one batched launch; per-stream airlight state and
+ * scratch stay resident on the device. */
+
+/* Admit a stream of W x H frames. HZ_EBUSY if its resident footprint does
+ * not fit the memory budget / free device memory. */
+hz_status hz_open_stream(hz_ctx* ctx, int32_t W, int32_t H, uint32_t flags, int32_t* stream_id);
+hz_status hz_close_stream(hz_ctx* ctx, int32_t stream_id);
+
+/* Queue one frame of a stream. in/out: host memory (pinned for overlap) when
+ * flags has HZ_IO_HOST, else device memory. The buffers must stay valid until
+ * hz_poll returns HZ_OK for the ticket. Thread-safe. */
+hz_status hz_submit(hz_ctx* ctx, int32_t stream_id, const uint8_t* in, size_t in_pitch,
+                    uint8_t* out, size_t out_pitch, uint32_t flags, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = just test, < 0 = forever) for a ticket:
+ * HZ_OK (done; info filled if not NULL), HZ_EAGAIN (timeout_us == 0 and not
+ * done), HZ_ETIMEDOUT, or the frame's error. Thread-safe. */
+hz_status hz_poll(hz_ctx* ctx, uint64_t ticket, int64_t timeout_us, hz_frame_info* info);
+
+/* Per-stream state (airlight EMA and frame count), HZ_STREAM_STATE_BYTES
+ * bytes, for resuming a stream after a restart. */
+#define HZ_STREAM_STATE_BYTES 48
+hz_status hz_stream_get_state(hz_ctx* ctx, int32_t stream_id, void* buf, size_t size);
+hz_status hz_stream_set_state(hz_ctx* ctx, int32_t stream_id, const void* buf, size_t size);
+
+/* Serving statistics since the context was created. Latency is measured from
+ * hz_submit to the completion of the frame's output copy. */
+typedef struct hz_server_stats {
+  uint64_t frames_done;
+  uint64_t batches;
+  double p50_ms;
+  double p99_ms;
+  double mean_ms;
+  double max_ms;
+  double busy_s;       /* wall time from the first submit to the last completion */
+} hz_server_stats;
+hz_status hz_get_server_stats(hz_ctx* ctx, hz_server_stats* out);
+
+/* ---------------------------------------------------------- profiling -- */
+/* Kernel classes of the path, for launch counts and timing. */
+enum {
+  HZ_K_DARK = 0,      /* dark channel tiles: per-channel patch minima (Eq. 2) */
+  HZ_K_SELECT = 1,    /* top-K selection and A_hat (Eq. 3) */
+  HZ_K_AIRLIGHT = 2,  /* airlight finish: override / smoothing */
+  HZ_K_RECON = 3,     /* transmission + reconstruction + gamma (Eq. 4-5, 7-8) */
+  HZ_K_BALANCE = 4,   /* colour-balance statistics pass */
+  HZ_K_TRANS = 5,     /* transmission plane only (image mode, stage call) */
+  HZ_K_GUIDED = 6,    /* guided-filter passes (Eq. 6) */
+  HZ_K_FUSED = 7,     /* persistent fused pipeline */
+  HZ_K_COUNT = 8
+};
+
+typedef struct hz_profile {
+  uint64_t launches[HZ_K_COUNT];  /* kernels launched, per class (always counted) */
+  uint64_t timed[HZ_K_COUNT];     /* launches timed while profiling was on */
+  double ms[HZ_K_COUNT];          /* summed device time of the timed launches */
+} hz_profile;
+
+/* Turn per-launch timing on or off: when on, every kernel launch is
+ * bracketed by a pair of CUDA events on its stream. */
+hz_status hz_set_profiling(hz_ctx* ctx, int on);
+/* Wait for the context's work, fold finished event pairs into the totals,
+ * copy them to *out and, if reset != 0, clear them. */
+hz_status hz_get_profile(hz_ctx* ctx, hz_profile* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HAZEDEFY_H */

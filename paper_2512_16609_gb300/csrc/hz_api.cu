@@ -1,0 +1,857 @@
+// C interface of the Hazedefy library (declared in include/hazedefy.h):
+// context and parameters, the video/batch/image paths and the stage calls.
+#include <cmath>
+
+#include "hz_guided.cuh"
+#include "hz_kernels.cuh"
+#include "hz_runtime.cuh"
+
+namespace hz {
+
+HzKParams kparams_of(const hz_params& p) {
+  HzKParams k{};
+  k.omega = p.omega;
+  k.t0 = p.t0;
+  k.alpha = p.alpha;
+  k.gamma_inv = float(1.0 / double(p.gamma));
+  k.gamma_is_one = (p.gamma == 1.0f) ? 1 : 0;
+  k.ema = p.airlight_ema;
+  for (int c = 0; c < 3; ++c) k.ov[c] = p.airlight_override[c];
+  k.use_override = p.use_airlight_override;
+  k.t_fast = (p.t_mode == HZ_T_FAST) ? 1 : 0;
+  return k;
+}
+
+hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s) {
+  if (bytes <= a.cap) return HZ_OK;
+  size_t want = align_up(bytes + bytes / 8, size_t(1) << 20);
+  const size_t others = c->arena.cap + c->stage.cap + c->resident_bytes - a.cap;
+  if (c->budget && others + want > c->budget) {
+    want = bytes;
+    if (others + want > c->budget)
+      return fail(c, HZ_ENOMEM, "scratch of %zu bytes exceeds the memory budget of %zu bytes", bytes, c->budget);
+  }
+  if (a.base) {
+    HZ_CK(c, cudaStreamSynchronize(s));
+    HZ_CK(c, cudaFree(a.base));
+    a.base = nullptr;
+    a.cap = 0;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HZ_ENOMEM, "cudaMalloc of %zu bytes failed", want);
+  }
+  a.base = static_cast<uint8_t*>(p);
+  a.cap = want;
+  return HZ_OK;
+}
+
+template <int R>
+static cudaError_t set_attr_one() {
+  return cudaFuncSetAttribute(k_p1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, P1G<R>::SMEM);
+}
+
+hz_status set_p1_attributes(hz_ctx* c) {
+  HZ_CK(c, set_attr_one<0>());  HZ_CK(c, set_attr_one<1>());  HZ_CK(c, set_attr_one<2>());
+  HZ_CK(c, set_attr_one<3>());  HZ_CK(c, set_attr_one<4>());  HZ_CK(c, set_attr_one<5>());
+  HZ_CK(c, set_attr_one<6>());  HZ_CK(c, set_attr_one<7>());  HZ_CK(c, set_attr_one<8>());
+  HZ_CK(c, set_attr_one<9>());  HZ_CK(c, set_attr_one<10>()); HZ_CK(c, set_attr_one<11>());
+  HZ_CK(c, set_attr_one<12>()); HZ_CK(c, set_attr_one<13>()); HZ_CK(c, set_attr_one<14>());
+  HZ_CK(c, set_attr_one<15>());
+  return HZ_OK;
+}
+
+hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& jobs) {
+  LaunchScope ls(c, HZ_K_DARK, s);
+  switch (R) {
+#define HZ_P1_CASE(r) \
+  case r: k_p1<r><<<grid, P1_THREADS, P1G<r>::SMEM, s>>>(jobs); break;
+    HZ_P1_CASE(0) HZ_P1_CASE(1) HZ_P1_CASE(2) HZ_P1_CASE(3) HZ_P1_CASE(4) HZ_P1_CASE(5)
+    HZ_P1_CASE(6) HZ_P1_CASE(7) HZ_P1_CASE(8) HZ_P1_CASE(9) HZ_P1_CASE(10) HZ_P1_CASE(11)
+    HZ_P1_CASE(12) HZ_P1_CASE(13) HZ_P1_CASE(14) HZ_P1_CASE(15)
+#undef HZ_P1_CASE
+    default:
+      return fail(c, HZ_EINVAL, "patch radius %d out of range", R);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status order_after_previous(hz_ctx* c, cudaStream_t s) {
+  if (c->have_done) HZ_CK(c, cudaStreamWaitEvent(s, c->done_ev, 0));
+  return HZ_OK;
+}
+
+hz_status mark_done(hz_ctx* c, cudaStream_t s) {
+  HZ_CK(c, cudaEventRecord(c->done_ev, s));
+  c->have_done = true;
+  return HZ_OK;
+}
+
+void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video) {
+  jobs.n = n;
+  uint8_t* A = c->arena.base;
+  for (int i = 0; i < n; ++i) {
+    const FramePlan& f = lp.fp[i];
+    HzJob& j = jobs.j[i];
+    j = HzJob{};
+    j.in = fr[i].in;
+    j.out = fr[i].out;
+    j.in_pitch = (long long)fr[i].in_pitch;
+    j.out_pitch = (long long)fr[i].out_pitch;
+    j.W = f.W;
+    j.H = f.H;
+    j.tiles_x = f.tiles_x;
+    j.tiles_y = f.tiles_y;
+    j.segs = f.segs;
+    j.tsrc = tsrc_video;
+    j.K = f.K;
+    j.P = A + f.off_P;
+    j.P_pitch = f.P_pitch;
+    j.Dout = nullptr;
+    j.D_pitch = 0;
+    j.tilemax = A + f.off_tilemax;
+    j.rowcnt = reinterpret_cast<unsigned*>(A + f.off_rowcnt);
+    j.rowsum = reinterpret_cast<unsigned*>(A + f.off_rowsum);
+    j.rec = reinterpret_cast<HzFrameRec*>(A + f.off_rec);
+    j.bal_part = f.off_bal ? reinterpret_cast<double*>(A + f.off_bal) : nullptr;
+    j.tplane = nullptr;
+    j.t_pitch = 0;
+    const int sid = fr[i].stream_id;
+    j.state = (sid >= 0 && sid < MAX_STREAMS) ? c->states + sid : nullptr;
+    j.use_override = c->prm.use_airlight_override;
+    j.t_half_out = 0;
+  }
+}
+
+static int max_tiles(const HzJobs& jobs) {
+  int m = 1;
+  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].tiles_x * jobs.j[i].tiles_y);
+  return m;
+}
+
+static int max_units(const HzJobs& jobs) {
+  int m = 1;
+  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].H * jobs.j[i].segs);
+  return m;
+}
+
+// dark channel + selection + airlight finish
+static hz_status run_front(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, cudaStream_t s) {
+  const HzKParams kp = kparams_of(c->prm);
+  HZ_CK(c, cudaMemsetAsync(c->arena.base, 0, lp.zero_bytes, s));
+  const dim3 g1(max_tiles(jobs), jobs.n);
+  hz_status st = launch_p1(c, c->prm.patch / 2, g1, s, jobs);
+  if (st != HZ_OK) return st;
+  {
+    LaunchScope ls(c, HZ_K_SELECT, s);
+    k_p2<<<g1, 256, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  {
+    LaunchScope ls(c, HZ_K_AIRLIGHT, s);
+    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return HZ_OK;
+}
+
+static hz_status run_recon(hz_ctx* c, HzJobs& jobs, bool balance, cudaStream_t s) {
+  const HzKParams kp = kparams_of(c->prm);
+  const dim3 g3(max_units(jobs), jobs.n);
+  if (balance) {
+    {
+      LaunchScope ls(c, HZ_K_BALANCE, s);
+      k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+    }
+    HZ_CK(c, cudaGetLastError());
+    LaunchScope ls(c, HZ_K_RECON, s);
+    k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+  } else {
+    LaunchScope ls(c, HZ_K_RECON, s);
+    k_p3<M_OUT><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s) {
+  hz_status st = run_front(c, lp, jobs, s);
+  if (st != HZ_OK) return st;
+  return run_recon(c, jobs, balance, s);
+}
+
+static hz_status run_guided(hz_ctx* c, GfArgs& g, cudaStream_t s) {
+  const dim3 gv((g.W + GF_VCOLS - 1) / GF_VCOLS, (g.H + GF_VBAND - 1) / GF_VBAND);
+  const dim3 gh((g.W + GF_HSEG - 1) / GF_HSEG, g.H);
+  const size_t sm1 = sizeof(float) * 4 * (GF_HSEG + 2 * g.r);
+  const size_t sm2 = sizeof(float) * 2 * (GF_HSEG + 2 * g.r);
+  HZ_CK(c, cudaFuncSetAttribute(k_gf_h<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  HZ_CK(c, cudaFuncSetAttribute(k_gf_h<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+  {
+    LaunchScope ls(c, HZ_K_GUIDED, s);
+    k_gf_v<1><<<gv, GF_VCOLS, 0, s>>>(g);
+  }
+  HZ_CK(c, cudaGetLastError());
+  {
+    LaunchScope ls(c, HZ_K_GUIDED, s);
+    k_gf_h<1><<<gh, GF_HSEG / GF_HRUN, sm1, s>>>(g);
+  }
+  HZ_CK(c, cudaGetLastError());
+  {
+    LaunchScope ls(c, HZ_K_GUIDED, s);
+    k_gf_v<2><<<gv, GF_VCOLS, 0, s>>>(g);
+  }
+  HZ_CK(c, cudaGetLastError());
+  {
+    LaunchScope ls(c, HZ_K_GUIDED, s);
+    k_gf_h<2><<<gh, GF_HSEG / GF_HRUN, sm2, s>>>(g);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return HZ_OK;
+}
+
+hz_status run_image_job(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s) {
+  hz_status st = run_front(c, lp, jobs, s);
+  if (st != HZ_OK) return st;
+  const HzKParams kp = kparams_of(c->prm);
+  const bool h = c->prm.precision == HZ_PREC_FP16;
+  const FramePlan& f = lp.fp[0];
+  HzJob& j = jobs.j[0];
+  uint8_t* A = c->arena.base;
+  const long long pp = h ? f.plane_pitch16 : f.plane_pitch32;
+  // coarse t plane
+  j.tplane = A + f.off_t;
+  j.t_pitch = pp;
+  j.t_half_out = h ? 1 : 0;
+  j.tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  const dim3 g3(max_units(jobs), 1);
+  {
+    LaunchScope ls(c, HZ_K_TRANS, s);
+    k_p3<M_T_ONLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  // guided filter
+  GfArgs g{};
+  g.in = j.in;
+  g.in_pitch = j.in_pitch;
+  g.W = f.W;
+  g.H = f.H;
+  g.r = c->prm.gf_radius;
+  g.eps = c->prm.gf_eps;
+  g.t0 = c->prm.t0;
+  g.clamp = 1;
+  g.p = A + f.off_t;
+  g.p_pitch = pp;
+  g.p_half = h;
+  g.vs = reinterpret_cast<float*>(A + f.off_vs);
+  g.a = A + f.off_a;
+  g.b = A + f.off_b;
+  g.ab_pitch = pp;
+  g.ab_half = h;
+  g.q = A + f.off_q;
+  g.q_pitch = pp;
+  g.q_half = h;
+  st = run_guided(c, g, s);
+  if (st != HZ_OK) return st;
+  // reconstruction with the refined t
+  j.tplane = A + f.off_q;
+  j.tsrc = h ? TS_PLANE16 : TS_PLANE32;
+  return run_recon(c, jobs, balance, s);
+}
+
+hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_frame_info* infos, bool balance) {
+  if (!infos) return HZ_OK;
+  for (int i = 0; i < n; ++i)
+    HZ_CK(c, cudaMemcpyAsync(c->rec_host + i, c->arena.base + lp.fp[i].off_rec, sizeof(HzFrameRec),
+                             cudaMemcpyDeviceToHost, s));
+  HZ_CK(c, cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i) {
+    const HzFrameRec& r = c->rec_host[i];
+    hz_frame_info& o = infos[i];
+    std::memset(&o, 0, sizeof o);
+    for (int k = 0; k < 3; ++k) {
+      o.A[k] = r.A[k];
+      o.A_hat[k] = float(r.A_hat[k]);
+      o.S[k] = (int64_t)r.S[k];
+      o.gains[k] = balance ? r.gains[k] : 1.f;
+      o.mean_jg[k] = balance ? r.mean_jg[k] : 0.f;
+    }
+    o.K = lp.fp[i].K;
+    o.n_above = r.n_above;
+    o.cut_index = r.cut_index;
+    o.T = r.T;
+    o.status = r.status;
+  }
+  return HZ_OK;
+}
+
+}  // namespace hz
+
+using namespace hz;
+
+// --------------------------------------------------------------- params --
+
+extern "C" void hz_params_default(hz_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->struct_size = sizeof(hz_params);
+  p->patch = 15;
+  p->omega = 0.95f;
+  p->t0 = 0.1f;
+  p->top_fraction = 0.001f;
+  p->alpha = 0.8f;
+  p->gamma = 1.2f;
+  p->t_mode = HZ_T_DCP;
+  p->color_balance = 0;
+  p->airlight_ema = 0.f;
+  p->gf_radius = 60;
+  p->gf_eps = 1e-3f;
+  p->precision = HZ_PREC_FP32;
+  p->use_airlight_override = 0;
+  p->airlight_override[0] = p->airlight_override[1] = p->airlight_override[2] = 1.f;
+}
+
+static bool finite_in(float v, float lo, float hi) { return std::isfinite(v) && v >= lo && v <= hi; }
+
+static hz_status validate(hz_ctx* c, const hz_params* p) {
+  if (!p) return fail(c, HZ_EINVAL, "params is NULL");
+  if (p->struct_size != sizeof(hz_params))
+    return fail(c, HZ_EINVAL, "struct_size %u != %zu", p->struct_size, sizeof(hz_params));
+  if (p->patch < 1 || p->patch > HZ_MAX_PATCH || (p->patch % 2) == 0)
+    return fail(c, HZ_EINVAL, "patch must be odd in [1, %d]", HZ_MAX_PATCH);
+  if (!finite_in(p->omega, 0.f, 1.f)) return fail(c, HZ_EINVAL, "omega must be in [0, 1]");
+  if (!finite_in(p->t0, 0.f, 0.999f)) return fail(c, HZ_EINVAL, "t0 must be in [0, 1)");
+  if (!(p->top_fraction > 0.f) || !(p->top_fraction <= 1.f)) return fail(c, HZ_EINVAL, "top_fraction must be in (0, 1]");
+  if (!(p->alpha > 0.f) || !(p->alpha <= 4.f)) return fail(c, HZ_EINVAL, "alpha must be in (0, 4]");
+  if (!(p->gamma > 0.f) || !std::isfinite(p->gamma) || p->gamma > 100.f) return fail(c, HZ_EINVAL, "gamma must be in (0, 100]");
+  if (p->t_mode != HZ_T_DCP && p->t_mode != HZ_T_FAST) return fail(c, HZ_EINVAL, "t_mode");
+  if (p->color_balance != 0 && p->color_balance != 1) return fail(c, HZ_EINVAL, "color_balance must be 0 or 1");
+  if (!(p->airlight_ema >= 0.f) || !(p->airlight_ema < 1.f)) return fail(c, HZ_EINVAL, "airlight_ema must be in [0, 1)");
+  if (p->gf_radius < 1 || p->gf_radius > HZ_MAX_GF_RADIUS) return fail(c, HZ_EINVAL, "gf_radius must be in [1, %d]", HZ_MAX_GF_RADIUS);
+  if (!(p->gf_eps >= 0.f) || !std::isfinite(p->gf_eps)) return fail(c, HZ_EINVAL, "gf_eps must be >= 0");
+  if (p->precision != HZ_PREC_FP32 && p->precision != HZ_PREC_FP16) return fail(c, HZ_EINVAL, "precision");
+  if (p->use_airlight_override != 0 && p->use_airlight_override != 1) return fail(c, HZ_EINVAL, "use_airlight_override");
+  if (p->use_airlight_override)
+    for (int k = 0; k < 3; ++k)
+      if (!(p->airlight_override[k] > 0.f) || !(p->airlight_override[k] <= 1.f))
+        return fail(c, HZ_EINVAL, "airlight_override must be in (0, 1]");
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_params_validate(const hz_params* p) { return validate(nullptr, p); }
+
+extern "C" const char* hz_status_str(hz_status s) {
+  switch (s) {
+    case HZ_OK: return "HZ_OK";
+    case HZ_EAGAIN: return "HZ_EAGAIN: not finished";
+    case HZ_EINVAL: return "HZ_EINVAL: invalid argument";
+    case HZ_ENOMEM: return "HZ_ENOMEM: out of memory";
+    case HZ_EBUSY: return "HZ_EBUSY: admission refused";
+    case HZ_ETIMEDOUT: return "HZ_ETIMEDOUT: timed out";
+    case HZ_ECUDA: return "HZ_ECUDA: CUDA error";
+    case HZ_EDEVICE_TIMEOUT: return "HZ_EDEVICE_TIMEOUT: device wait gave up";
+    case HZ_ESTATE: return "HZ_ESTATE: invalid state";
+  }
+  return "unknown hz_status";
+}
+
+extern "C" const char* hz_last_error(const hz_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+extern "C" hz_status hz_create(const hz_params* p, int device, size_t mem_budget_bytes, hz_ctx** out) {
+  if (!out) return HZ_EINVAL;
+  *out = nullptr;
+  hz_params def;
+  if (!p) {
+    hz_params_default(&def);
+    p = &def;
+  }
+  hz_status st = validate(nullptr, p);
+  if (st != HZ_OK) return st;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return HZ_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return HZ_ECUDA;
+  hz_ctx* c = new (std::nothrow) hz_ctx();
+  if (!c) return HZ_ENOMEM;
+  c->prm = *p;
+  c->device = device;
+  c->budget = mem_budget_bytes;
+  bool ok = cudaMalloc(&c->states, sizeof(HzStreamState) * (MAX_STREAMS + 1)) == cudaSuccess &&
+            cudaMemset(c->states, 0, sizeof(HzStreamState) * (MAX_STREAMS + 1)) == cudaSuccess &&
+            cudaMallocHost(&c->rec_host, sizeof(HzFrameRec) * MAXJ) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; ok && i < 2; ++i)
+    ok = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = set_p1_attributes(c) == HZ_OK;
+  if (!ok) {
+    cudaGetLastError();
+    hz_destroy(c);
+    return HZ_ECUDA;
+  }
+  *out = c;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_destroy(hz_ctx* c) {
+  if (!c) return HZ_OK;
+  cudaSetDevice(c->device);
+  server_stop(c);
+  cudaDeviceSynchronize();
+  if (c->arena.base) cudaFree(c->arena.base);
+  if (c->stage.base) cudaFree(c->stage.base);
+  if (c->states) cudaFree(c->states);
+  if (c->rec_host) cudaFreeHost(c->rec_host);
+  if (c->done_ev) cudaEventDestroy(c->done_ev);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
+    if (c->ev_out[i]) cudaEventDestroy(c->ev_out[i]);
+  }
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->copy_in) cudaStreamDestroy(c->copy_in);
+  if (c->copy_out) cudaStreamDestroy(c->copy_out);
+  cudaGetLastError();
+  delete c;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_params(const hz_ctx* c, hz_params* out) {
+  if (!c || !out) return HZ_EINVAL;
+  *out = c->prm;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_set_params(hz_ctx* c, const hz_params* p) {
+  if (!c) return HZ_EINVAL;
+  hz_status st = validate(c, p);
+  if (st != HZ_OK) return st;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->prm = *p;
+  return HZ_OK;
+}
+
+// ------------------------------------------------------------- checks --
+
+static hz_status check_frame(hz_ctx* c, const void* in, int W, int H, size_t pitch, const void* out,
+                             size_t opitch, bool need_out) {
+  if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || (long long)W * H > (1LL << 28))
+    return fail(c, HZ_EINVAL, "frame size %dx%d out of range", W, H);
+  if (!in) return fail(c, HZ_EINVAL, "input pointer is NULL");
+  if (pitch < size_t(3) * W) return fail(c, HZ_EINVAL, "in_pitch %zu < 3*W", pitch);
+  if (need_out) {
+    if (!out) return fail(c, HZ_EINVAL, "output pointer is NULL");
+    if (opitch < size_t(3) * W) return fail(c, HZ_EINVAL, "out_pitch %zu < 3*W", opitch);
+  }
+  return HZ_OK;
+}
+
+#define HZ_TRY(expr)                  \
+  do {                                \
+    hz_status st_ = (expr);           \
+    if (st_ != HZ_OK) return st_;     \
+  } while (0)
+
+static hz_status check_stream_id(hz_ctx* c, int32_t sid) {
+  if (sid == -1) return HZ_OK;
+  if (sid < 0 || sid >= MAX_STREAMS) return fail(c, HZ_EINVAL, "stream_id %d out of range", sid);
+  std::lock_guard<std::mutex> lk(c->smu);
+  if (!c->stream_open[sid]) return fail(c, HZ_ESTATE, "stream %d is not open", sid);
+  return HZ_OK;
+}
+
+// Video frames on device memory, chunked by MAXJ and an L2-sized wave.
+static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
+                              HzStreamState* chain) {
+  const bool bal = c->prm.color_balance != 0;
+  const int tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  int i = 0;
+  while (i < n) {
+    // frames per launch: up to MAXJ, and about 48 MB of input per wave so the
+    // second read of each frame is served from L2
+    size_t bytes = 0;
+    int m = 0;
+    while (i + m < n && m < MAXJ) {
+      const size_t fb = size_t(3) * fr[i + m].W * fr[i + m].H;
+      if (m > 0 && bytes + fb > (size_t(48) << 20)) break;
+      bytes += fb;
+      ++m;
+    }
+    std::vector<int> Ws(m), Hs(m);
+    for (int k = 0; k < m; ++k) {
+      Ws[k] = fr[i + k].W;
+      Hs[k] = fr[i + k].H;
+    }
+    LaunchPlan lp;
+    plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp);
+    HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+    HzJobs jobs;
+    fill_jobs(c, lp, fr + i, m, jobs, tsrc);
+    if (chain)
+      for (int k = 0; k < m; ++k) jobs.j[k].state = chain;
+    HZ_TRY(run_video_jobs(c, lp, jobs, bal, s));
+    HZ_TRY(read_infos(c, lp, m, s, infos ? infos + i : nullptr, bal));
+    i += m;
+  }
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_dehaze_frame(hz_ctx* c, int32_t stream_id, const uint8_t* in, int32_t W, int32_t H,
+                                     size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
+                                     hz_frame_info* info) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  HZ_TRY(check_stream_id(c, stream_id));
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, stream_id, 0u};
+  HZ_TRY(video_device(c, &d, 1, s, info, nullptr));
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
+                                     hz_frame_info* infos) {
+  if (!c) return HZ_EINVAL;
+  if (n < 0 || (n > 0 && !frames)) return fail(c, HZ_EINVAL, "bad frame list");
+  for (int i = 0; i < n; ++i) {
+    HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
+                       frames[i].out_pitch, true));
+    HZ_TRY(check_stream_id(c, frames[i].stream_id));
+  }
+  if (n == 0) return HZ_OK;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  // guided frames go one by one through the image path; the rest batched
+  std::vector<hz_frame_desc> plain;
+  std::vector<int> plain_idx;
+  for (int i = 0; i < n; ++i) {
+    if (frames[i].flags & HZ_GUIDED) continue;
+    plain.push_back(frames[i]);
+    plain_idx.push_back(i);
+  }
+  std::vector<hz_frame_info> pinfo(plain.size());
+  if (!plain.empty())
+    HZ_TRY(video_device(c, plain.data(), (int)plain.size(), s, infos ? pinfo.data() : nullptr, nullptr));
+  if (infos)
+    for (size_t k = 0; k < plain.size(); ++k) infos[plain_idx[k]] = pinfo[k];
+  const bool bal = c->prm.color_balance != 0;
+  for (int i = 0; i < n; ++i) {
+    if (!(frames[i].flags & HZ_GUIDED)) continue;
+    LaunchPlan lp;
+    plan_frames(c->prm, &frames[i].W, &frames[i].H, 1, true, bal, lp);
+    HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+    HzJobs jobs;
+    fill_jobs(c, lp, frames + i, 1, jobs, TS_P);
+    HZ_TRY(run_image_job(c, lp, jobs, bal, s));
+    HZ_TRY(read_infos(c, lp, 1, s, infos ? infos + i : nullptr, bal));
+  }
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t* in, int32_t n_frames,
+                                     int32_t W, int32_t H, size_t in_pitch, size_t in_frame_stride, uint8_t* out,
+                                     size_t out_pitch, size_t out_frame_stride, uint32_t flags,
+                                     void* cuda_stream, hz_frame_info* infos) {
+  if (!c) return HZ_EINVAL;
+  if (n_frames < 0) return fail(c, HZ_EINVAL, "n_frames < 0");
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  HZ_TRY(check_stream_id(c, stream_id));
+  if (flags & ~uint32_t(HZ_IO_HOST)) return fail(c, HZ_EINVAL, "unknown flags");
+  if (n_frames > 1 && (in_frame_stride < in_pitch * size_t(H - 1) + size_t(3) * W ||
+                       out_frame_stride < out_pitch * size_t(H - 1) + size_t(3) * W))
+    return fail(c, HZ_EINVAL, "frame stride smaller than a frame");
+  if (n_frames == 0) return HZ_OK;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  // the smoothing chain runs through the stream's state, or a call-local one
+  HzStreamState* chain = nullptr;
+  if (stream_id < 0) {
+    chain = c->states + MAX_STREAMS;
+    HZ_CK(c, cudaMemsetAsync(chain, 0, sizeof(HzStreamState), s));
+  }
+  if (!(flags & HZ_IO_HOST)) {
+    std::vector<hz_frame_desc> fr(n_frames);
+    for (int f = 0; f < n_frames; ++f)
+      fr[f] = hz_frame_desc{in + size_t(f) * in_frame_stride, in_pitch, out + size_t(f) * out_frame_stride,
+                            out_pitch, W, H, stream_id, 0u};
+    HZ_TRY(video_device(c, fr.data(), n_frames, s, infos, chain));
+    return mark_done(c, s);
+  }
+  // host buffers: waves of frames staged through two device buffer pairs;
+  // H2D of wave k+1 (copy_in) and D2H of wave k-1 (copy_out) overlap the
+  // compute of wave k (s).
+  const size_t fin = size_t(3) * W * H, fout = fin;
+  int G = (int)std::max<size_t>(1, (size_t(48) << 20) / std::max<size_t>(fin, 1));
+  G = std::min(G, MAXJ);
+  G = std::min(G, n_frames);
+  const size_t half = align_up(size_t(G) * (fin + fout), 4096);
+  HZ_TRY(arena_reserve(c, c->stage, 2 * half, s));
+  HZ_CK(c, cudaEventRecord(c->ev_comp[0], s));
+  HZ_CK(c, cudaStreamWaitEvent(c->copy_in, c->ev_comp[0], 0));
+  HZ_CK(c, cudaStreamWaitEvent(c->copy_out, c->ev_comp[0], 0));
+  const int nw = (n_frames + G - 1) / G;
+  bool out_pending[2] = {false, false};
+  for (int w = 0; w < nw; ++w) {
+    const int b = w & 1;
+    const int f0 = w * G, m = std::min(G, n_frames - f0);
+    uint8_t* din = c->stage.base + b * half;
+    uint8_t* dout = din + size_t(G) * fin;
+    // the buffer pair b is free once its previous D2H finished
+    if (out_pending[b]) HZ_CK(c, cudaStreamWaitEvent(c->copy_in, c->ev_out[b], 0));
+    for (int k = 0; k < m; ++k)
+      HZ_CK(c, cudaMemcpy2DAsync(din + size_t(k) * fin, size_t(3) * W, in + size_t(f0 + k) * in_frame_stride,
+                                 in_pitch, size_t(3) * W, H, cudaMemcpyHostToDevice, c->copy_in));
+    HZ_CK(c, cudaEventRecord(c->ev_in[b], c->copy_in));
+    HZ_CK(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
+    std::vector<hz_frame_desc> fr(m);
+    for (int k = 0; k < m; ++k)
+      fr[k] = hz_frame_desc{din + size_t(k) * fin, size_t(3) * W, dout + size_t(k) * fout, size_t(3) * W, W, H,
+                            stream_id, 0u};
+    HZ_TRY(video_device(c, fr.data(), m, s, infos ? infos + f0 : nullptr, chain));
+    HZ_CK(c, cudaEventRecord(c->ev_comp[b], s));
+    HZ_CK(c, cudaStreamWaitEvent(c->copy_out, c->ev_comp[b], 0));
+    for (int k = 0; k < m; ++k)
+      HZ_CK(c, cudaMemcpy2DAsync(out + size_t(f0 + k) * out_frame_stride, out_pitch, dout + size_t(k) * fout,
+                                 size_t(3) * W, size_t(3) * W, H, cudaMemcpyDeviceToHost, c->copy_out));
+    HZ_CK(c, cudaEventRecord(c->ev_out[b], c->copy_out));
+    out_pending[b] = true;
+  }
+  // the call's stream completes after the last copy out
+  for (int b = 0; b < 2; ++b)
+    if (out_pending[b]) HZ_CK(c, cudaStreamWaitEvent(s, c->ev_out[b], 0));
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                     uint8_t* out, size_t out_pitch, void* cuda_stream, hz_frame_info* info) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  const bool bal = c->prm.color_balance != 0;
+  LaunchPlan lp;
+  plan_frames(c->prm, &W, &H, 1, true, bal, lp);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, -1, HZ_GUIDED};
+  HzJobs jobs;
+  fill_jobs(c, lp, &d, 1, jobs, TS_P);
+  HZ_TRY(run_image_job(c, lp, jobs, bal, s));
+  HZ_TRY(read_infos(c, lp, 1, s, info, bal));
+  return mark_done(c, s);
+}
+
+// ---------------------------------------------------------- stage calls --
+
+extern "C" hz_status hz_dark_channel(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                     uint8_t* D, size_t D_pitch, void* cuda_stream) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, nullptr, 0, false));
+  if (!D || D_pitch < size_t(W)) return fail(c, HZ_EINVAL, "bad D buffer");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  LaunchPlan lp;
+  plan_frames(c->prm, &W, &H, 1, false, false, lp);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  HzJobs jobs;
+  fill_jobs(c, lp, &d, 1, jobs, TS_P);
+  jobs.j[0].Dout = D;
+  jobs.j[0].D_pitch = (long long)D_pitch;
+  HZ_CK(c, cudaMemsetAsync(c->arena.base, 0, lp.zero_bytes, s));
+  HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(jobs.j[0].tiles_x * jobs.j[0].tiles_y, 1), s, jobs));
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_estimate_airlight(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                          void* cuda_stream, hz_frame_info* info) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, nullptr, 0, false));
+  if (!info) return fail(c, HZ_EINVAL, "info is NULL");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  LaunchPlan lp;
+  plan_frames(c->prm, &W, &H, 1, false, false, lp);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  HzJobs jobs;
+  fill_jobs(c, lp, &d, 1, jobs, TS_P);
+  jobs.j[0].use_override = 0;
+  HZ_TRY(run_front(c, lp, jobs, s));
+  HZ_TRY(read_infos(c, lp, 1, s, info, false));
+  return mark_done(c, s);
+}
+
+// Reconstruction-kernel launches that take A from the host.
+static hz_status stage_with_A(hz_ctx* c, const uint8_t* in, int W, int H, size_t in_pitch, const float* A,
+                              cudaStream_t s, LaunchPlan& lp, HzJobs& jobs, bool front) {
+  if (!A) return fail(c, HZ_EINVAL, "A is NULL");
+  for (int k = 0; k < 3; ++k)
+    if (!(A[k] > 0.f) || !(A[k] <= 1.f)) return fail(c, HZ_EINVAL, "A must be in (0, 1]");
+  plan_frames(c->prm, &W, &H, 1, false, c->prm.color_balance != 0, lp);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  fill_jobs(c, lp, &d, 1, jobs, TS_P);
+  jobs.j[0].use_override = 1;
+  HzKParams kp = kparams_of(c->prm);
+  for (int k = 0; k < 3; ++k) kp.ov[k] = A[k];
+  HZ_CK(c, cudaMemsetAsync(c->arena.base, 0, lp.zero_bytes, s));
+  if (front) {
+    HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(jobs.j[0].tiles_x * jobs.j[0].tiles_y, 1), s, jobs));
+  }
+  {
+    LaunchScope ls(c, HZ_K_AIRLIGHT, s);
+    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_transmission(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                     const float* A, float* t, size_t t_pitch, void* cuda_stream) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, nullptr, 0, false));
+  if (!t || t_pitch < sizeof(float) * W) return fail(c, HZ_EINVAL, "bad t buffer");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  LaunchPlan lp;
+  HzJobs jobs;
+  HZ_TRY(stage_with_A(c, in, W, H, in_pitch, A, s, lp, jobs, c->prm.t_mode == HZ_T_DCP));
+  jobs.j[0].tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  jobs.j[0].tplane = t;
+  jobs.j[0].t_pitch = (long long)t_pitch;
+  const HzKParams kp = kparams_of(c->prm);
+  {
+    LaunchScope ls(c, HZ_K_TRANS, s);
+    k_p3<M_T_ONLY><<<dim3(H * jobs.j[0].segs, 1), P3_THREADS, 0, s>>>(jobs, kp);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_recover(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                const float* t, size_t t_pitch, const float* A, uint8_t* out, size_t out_pitch,
+                                void* cuda_stream, hz_frame_info* info) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  if (!t || t_pitch < sizeof(float) * W) return fail(c, HZ_EINVAL, "bad t buffer");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  LaunchPlan lp;
+  HzJobs jobs;
+  HZ_TRY(stage_with_A(c, in, W, H, in_pitch, A, s, lp, jobs, false));
+  jobs.j[0].out = out;
+  jobs.j[0].out_pitch = (long long)out_pitch;
+  jobs.j[0].tsrc = TS_PLANE32;
+  jobs.j[0].tplane = const_cast<float*>(t);
+  jobs.j[0].t_pitch = (long long)t_pitch;
+  const bool bal = c->prm.color_balance != 0;
+  HZ_TRY(run_recon(c, jobs, bal, s));
+  HZ_TRY(read_infos(c, lp, 1, s, info, bal));
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_guided_filter(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
+                                      const float* p, size_t p_pitch, float* q, size_t q_pitch,
+                                      void* cuda_stream) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, nullptr, 0, false));
+  if (!p || !q || p_pitch < sizeof(float) * W || q_pitch < sizeof(float) * W)
+    return fail(c, HZ_EINVAL, "bad p/q planes");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  const size_t pp = align_up(sizeof(float) * W, 128);
+  const size_t need = 2 * pp * H + sizeof(float) * 4 * size_t(W) * H + 4096;
+  HZ_TRY(arena_reserve(c, c->arena, need, s));
+  GfArgs g{};
+  g.in = in;
+  g.in_pitch = (long long)in_pitch;
+  g.W = W;
+  g.H = H;
+  g.r = c->prm.gf_radius;
+  g.eps = c->prm.gf_eps;
+  g.t0 = 0.f;
+  g.clamp = 0;
+  g.p = p;
+  g.p_pitch = (long long)p_pitch;
+  g.p_half = 0;
+  g.a = c->arena.base;
+  g.b = c->arena.base + pp * H;
+  g.ab_pitch = (long long)pp;
+  g.ab_half = c->prm.precision == HZ_PREC_FP16 ? 1 : 0;
+  g.vs = reinterpret_cast<float*>(c->arena.base + align_up(2 * pp * H, 1024));
+  g.q = q;
+  g.q_pitch = (long long)q_pitch;
+  g.q_half = 0;
+  HZ_TRY(run_guided(c, g, s));
+  return mark_done(c, s);
+}
+
+// ------------------------------------------------------------ profiling --
+
+extern "C" hz_status hz_set_profiling(hz_ctx* c, int on) {
+  if (!c) return HZ_EINVAL;
+  std::lock_guard<std::mutex> lk(c->pmu);
+  c->prof = on != 0;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_profile(hz_ctx* c, hz_profile* out, int reset) {
+  if (!c || !out) return HZ_EINVAL;
+  cudaSetDevice(c->device);
+  HZ_CK(c, cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(c->pmu);
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.kind] += ms;
+      c->timed[p.kind] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  for (int k = 0; k < HZ_K_COUNT; ++k) {
+    out->launches[k] = c->launches[k];
+    out->timed[k] = c->timed[k];
+    out->ms[k] = c->prof_ms[k];
+  }
+  if (reset) {
+    for (int k = 0; k < HZ_K_COUNT; ++k) {
+      c->launches[k] = 0;
+      c->timed[k] = 0;
+      c->prof_ms[k] = 0.0;
+    }
+  }
+  return HZ_OK;
+}

@@ -1,0 +1,146 @@
+// Internal definitions shared by the Hazedefy kernels and the host runtime.
+//
+// Data layout in device memory (one frame):
+//   I    : caller's RGB u8 frame, H rows of 3W bytes at in_pitch.
+//   P    : per-channel patch minima P^c(x) = min_{y in patch(x)} I^c(y), RGB
+//          u8 interleaved like I, pitch a multiple of 128 bytes. Because the
+//          minimum commutes with min over c and with division by A^c > 0,
+//            D(x)                       = min_c P^c(x)          (Eq. 2)
+//            min_patch min_c I^c/A^c    = min_c P^c(x) / A^c    (t, DCP form)
+//          so P feeds the dark channel, the airlight selection and the
+//          transmission without a second min filter.
+//   rec  : one HzFrameRec per frame (histogram, counters, selection, A).
+//   rows : per-row tie counts and r/g/b sums for the raster-order cut.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+namespace hz {
+
+// ---- tiling of the dark-channel / selection kernels --------------------
+constexpr int P1_TW = 128;      // tile width in pixels (multiple of 32)
+constexpr int P1_TH = 32;       // tile height in rows
+constexpr int P1_THREADS = 256;
+// ---- pointwise reconstruction kernels ----------------------------------
+constexpr int P3_THREADS = 256;
+constexpr int P3_PX = 4;                        // pixels per thread
+constexpr int P3_SEG = P3_THREADS * P3_PX;      // pixels per block and row
+// ---- guided filter ------------------------------------------------------
+constexpr int GF_VBAND = 64;    // output rows per vertical-pass block
+constexpr int GF_VCOLS = 128;   // columns per vertical-pass block
+constexpr int GF_HSEG = 256;    // outputs per horizontal-pass block
+constexpr int GF_HRUN = 8;      // consecutive outputs per thread
+
+constexpr float A_FLOOR = 1e-6f;  // airlight floor used in ratios I/A
+constexpr int HZ_STATUS_SELECT_FAILED = -100;  // per-frame status: selection inconsistent
+
+// Per-frame record, zeroed before each launch that uses it.
+struct HzFrameRec {
+  unsigned hist[256];           // histogram of D
+  unsigned done_p1, done_p2, done_p3, done_pad;
+  int T;                        // threshold level
+  int status;
+  long long n_above;            // #(D > T)
+  long long m_ties;             // ties to take = K - n_above
+  unsigned long long S_above[3];
+  unsigned long long S[3];      // sums over the selected set
+  long long cut_index;
+  double A_hat[3];              // Eq. 3 estimate
+  double A_used[3];             // after override / smoothing
+  float A[3];                   // float copy used by kernels
+  float inv[3];                 // 1 / (255 * max(A^c, floor))
+  float inv_fast;               // 1 / (255 * max_c A^c)
+  float gains[3];
+  float mean_jg[3];
+  float pad2;
+};
+
+// Airlight smoothing state of one stream (48 bytes; matches the size the
+// C interface exports for checkpointing).
+struct HzStreamState {
+  double A[3];
+  long long frames;
+  double reserved[2];
+};
+static_assert(sizeof(HzStreamState) == 48, "stream state is 48 bytes");
+
+// Where the reconstruction kernel takes t from.
+enum TSource : int { TS_P = 0, TS_FAST = 1, TS_PLANE32 = 2, TS_PLANE16 = 3 };
+// What the reconstruction kernel produces.
+enum P3Mode : int { M_OUT = 0, M_BAL_SUMS = 1, M_BAL_APPLY = 2, M_T_ONLY = 3 };
+
+// One frame of a launch (read-only for the kernels).
+struct HzJob {
+  const uint8_t* in;
+  uint8_t* out;
+  long long in_pitch, out_pitch;
+  int W, H;
+  int tiles_x, tiles_y;         // dark-channel tiling
+  int segs;                     // reconstruction segments per row
+  int tsrc;                     // TSource for the reconstruction pass
+  long long K;
+  uint8_t* P;
+  long long P_pitch;
+  uint8_t* Dout;                // optional dark channel output
+  long long D_pitch;
+  uint8_t* tilemax;
+  unsigned* rowcnt;             // [H]
+  unsigned* rowsum;             // [3H]
+  HzFrameRec* rec;
+  double* bal_part;             // [H*segs*3] per-block partial sums
+  void* tplane;                 // t plane (output of M_T_ONLY / input)
+  long long t_pitch;            // bytes
+  HzStreamState* state;         // airlight smoothing chain (nullptr: none)
+  int use_override;
+  int t_half_out;               // M_T_ONLY writes an FP16 plane
+};
+
+constexpr int MAXJ = 64;  // frames per launch (jobs travel as a kernel parameter)
+struct HzJobs {
+  int n;
+  int pad;
+  HzJob j[MAXJ];
+};
+
+// Launch-wide scalar parameters.
+struct HzKParams {
+  float omega, t0, alpha, gamma_inv, ema;
+  float ov[3];
+  int use_override;
+  int gamma_is_one;
+  int t_fast;
+};
+
+// ---- small device helpers ----------------------------------------------
+
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) {
+  return __byte_perm(a, b, s);
+}
+
+// Load 4 bytes starting at any byte address p (reads the aligned words that
+// contain them).
+__device__ __forceinline__ uint32_t load_u32_unaligned(const uint8_t* p) {
+  uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  uint32_t sh = uint32_t(a & 3);
+  uint32_t lo = __ldg(w);
+  if (sh == 0) return lo;
+  uint32_t hi = __ldg(w + 1);
+  return __byte_perm(lo, hi, 0x3210 + 0x1111 * sh);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace hz

@@ -1,0 +1,224 @@
+// Host-side runtime of the Hazedefy library: context, scratch arena and the
+// launch planner shared by the video, batch, image and serving paths.
+#pragma once
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hazedefy.h"
+#include "hz_internal.cuh"
+
+namespace hz {
+
+constexpr int MAX_STREAMS = 256;
+
+struct Server;  // serving scheduler (hz_server.cu)
+
+// Grow-only device buffer.
+struct Arena {
+  uint8_t* base = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace hz
+
+struct hz_ctx {
+  hz_params prm;
+  int device = 0;
+  size_t budget = 0;          // 0 = unbounded
+  std::string err;
+  hz::Arena arena;            // per-call scratch
+  hz::Arena stage;            // device staging for host IO
+  hz::HzStreamState* states = nullptr;  // [MAX_STREAMS + 1]; last = call-local chain
+  hz::HzFrameRec* rec_host = nullptr;   // pinned, MAXJ records
+  cudaEvent_t done_ev = nullptr;        // end of the last call's work
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  bool have_done = false;
+  // stream table
+  std::mutex smu;
+  int stream_open[hz::MAX_STREAMS] = {0};
+  int stream_W[hz::MAX_STREAMS] = {0};
+  int stream_H[hz::MAX_STREAMS] = {0};
+  unsigned stream_flags[hz::MAX_STREAMS] = {0};
+  size_t stream_bytes[hz::MAX_STREAMS] = {0};
+  size_t resident_bytes = 0;
+  hz::Server* server = nullptr;
+  std::mutex call_mu;  // serialises the launch paths between the API and the server thread
+  // profiling
+  bool prof = false;
+  std::mutex pmu;
+  uint64_t launches[HZ_K_COUNT] = {0};
+  uint64_t timed[HZ_K_COUNT] = {0};
+  double prof_ms[HZ_K_COUNT] = {0};
+  std::vector<cudaEvent_t> ev_pool;
+  struct PendingTime { int kind; cudaEvent_t a, b; };
+  std::vector<PendingTime> pending;
+};
+
+namespace hz {
+
+inline hz_status fail(hz_ctx* c, hz_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define HZ_CK(ctx, call)                                                                \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::hz::fail((ctx), HZ_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+  } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Per-frame scratch plan.
+struct FramePlan {
+  int W, H, tiles_x, tiles_y, segs;
+  long long K;
+  long long P_pitch;
+  size_t off_rec, off_rowcnt, off_rowsum;  // in the zeroed region
+  size_t off_P, off_tilemax, off_bal;      // in the rest
+  size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
+  long long plane_pitch32, plane_pitch16;
+};
+
+struct LaunchPlan {
+  std::vector<FramePlan> fp;
+  size_t zero_bytes = 0;
+  size_t total = 0;
+};
+
+inline long long num_top(long long N, float frac) {
+  if (N <= 0) return 0;
+  const double k = std::floor(double(frac) * double(N));
+  long long K = (long long)k;
+  if (K < 1) K = 1;
+  if (K > N) K = N;
+  return K;
+}
+
+// image: add the guided-filter planes
+inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int n, bool image, bool balance,
+                        LaunchPlan& lp) {
+  lp.fp.resize(n);
+  size_t z = 0;
+  for (int i = 0; i < n; ++i) {
+    FramePlan& f = lp.fp[i];
+    f.W = Ws[i];
+    f.H = Hs[i];
+    f.tiles_x = (f.W + P1_TW - 1) / P1_TW;
+    f.tiles_y = (f.H + P1_TH - 1) / P1_TH;
+    f.segs = (f.W + P3_SEG - 1) / P3_SEG;
+    f.K = num_top((long long)f.W * f.H, prm.top_fraction);
+    f.P_pitch = (long long)align_up(size_t(3) * P1_TW * f.tiles_x, 128);
+    f.off_rec = z;
+    z = align_up(z + sizeof(HzFrameRec), 256);
+    f.off_rowcnt = z;
+    z = align_up(z + sizeof(unsigned) * f.H, 256);
+    f.off_rowsum = z;
+    z = align_up(z + sizeof(unsigned) * 3 * f.H, 256);
+  }
+  lp.zero_bytes = z;
+  size_t o = align_up(z, 1024);
+  for (int i = 0; i < n; ++i) {
+    FramePlan& f = lp.fp[i];
+    f.off_P = o;
+    o = align_up(o + size_t(f.P_pitch) * f.H, 1024);
+    f.off_tilemax = o;
+    o = align_up(o + size_t(f.tiles_x) * f.tiles_y, 256);
+    f.off_bal = 0;
+    if (balance) {
+      f.off_bal = o;
+      o = align_up(o + sizeof(double) * 3 * size_t(f.H) * f.segs, 256);
+    }
+    f.off_t = f.off_vs = f.off_a = f.off_b = f.off_q = 0;
+    f.plane_pitch32 = (long long)align_up(size_t(4) * f.W, 128);
+    f.plane_pitch16 = (long long)align_up(size_t(2) * f.W, 128);
+    if (image) {
+      const bool h = prm.precision == HZ_PREC_FP16;
+      const size_t pb = size_t(h ? f.plane_pitch16 : f.plane_pitch32) * f.H;
+      f.off_t = o;  o = align_up(o + pb, 1024);
+      f.off_a = o;  o = align_up(o + pb, 1024);
+      f.off_b = o;  o = align_up(o + pb, 1024);
+      f.off_q = o;  o = align_up(o + pb, 1024);
+      f.off_vs = o; o = align_up(o + sizeof(float) * 4 * size_t(f.W) * f.H, 1024);
+    }
+  }
+  lp.total = o;
+}
+
+// Counts a launch of `kind` and, while profiling is on, brackets it with
+// events on its stream.
+struct LaunchScope {
+  hz_ctx* c;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  LaunchScope(hz_ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    c->launches[kind] += 1;
+    if (c->prof) {
+      a = take_event();
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~LaunchScope() {
+    if (!a) return;
+    std::lock_guard<std::mutex> lk(c->pmu);
+    cudaEvent_t b = take_event();
+    if (!b) return;
+    cudaEventRecord(b, s);
+    c->pending.push_back({kind, a, b});
+  }
+  cudaEvent_t take_event() {
+    if (!c->ev_pool.empty()) {
+      cudaEvent_t e = c->ev_pool.back();
+      c->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+};
+
+hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s);
+hz_status set_p1_attributes(hz_ctx* c);
+HzKParams kparams_of(const hz_params& p);
+hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& jobs);
+hz_status order_after_previous(hz_ctx* c, cudaStream_t s);
+hz_status mark_done(hz_ctx* c, cudaStream_t s);
+
+// Build the jobs of one launch from a plan (device pointers inside arena).
+void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video);
+
+// Video-mode pipeline for up to MAXJ frames already described in `jobs`.
+hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s);
+// Image-mode pipeline for one frame.
+hz_status run_image_job(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s);
+// Copy records back (waits for the stream) and fill infos.
+hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_frame_info* infos, bool balance);
+
+// serving (hz_server.cu)
+void server_stop(hz_ctx* c);
+
+}  // namespace hz

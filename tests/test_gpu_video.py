@@ -1,0 +1,268 @@
+"""GPU parity of the video-mode path through the C interface against the FP64
+oracle: dark channel and selection bit-exact, transmission within 1e-6,
+uint8 output within 1 LSB."""
+import numpy as np
+import pytest
+
+import hazegen
+from oracle import hazedefy_oracle as O
+from tests.gpu_util import context, empty_dev, oracle_params, to_dev, torch, u8_diff
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(1, 1), (7, 5), (15, 17), (17, 15), (128, 32), (129, 33), (200, 150), (854, 480), (1023, 37)]
+
+
+def _img(W, H, seed, kind):
+    if kind == "haze":
+        return hazegen.make_frame(W, H, seed=seed, beta=1.0)
+    if kind == "levels":
+        return hazegen.random_u8_image(W, H, seed, levels=4) * 60
+    return hazegen.random_u8_image(W, H, seed)
+
+
+@pytest.mark.parametrize("W,H", SIZES)
+@pytest.mark.parametrize("patch", [1, 3, 15, 31])
+def test_dark_channel_bit_exact(W, H, patch):
+    I = _img(W, H, W * 7 + H + patch, "noise" if patch % 2 else "haze")
+    for pad in (0, 13):
+        with context(patch=patch) as (m, ctx):
+            It = to_dev(I, pad)
+            D = torch.full((H, W), 77, dtype=torch.uint8, device="cuda")
+            m.hz_dark_channel(ctx, It, D)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(D.cpu().numpy(), O.dark_channel(I, patch))
+
+
+@pytest.mark.parametrize("patch", [5, 7, 9, 11, 13, 17, 19, 21, 23, 25, 27, 29])
+def test_dark_channel_other_patches(patch):
+    I = _img(301, 77, patch, "haze")
+    with context(patch=patch) as (m, ctx):
+        D = torch.empty((77, 301), dtype=torch.uint8, device="cuda")
+        m.hz_dark_channel(ctx, to_dev(I), D)
+        np.testing.assert_array_equal(D.cpu().numpy(), O.dark_channel(I, patch))
+
+
+@pytest.mark.parametrize("W,H,kind,frac", [(200, 150, "haze", 0.001), (200, 150, "levels", 0.05),
+                                           (640, 480, "haze", 0.001), (33, 9, "levels", 1.0),
+                                           (33, 9, "noise", 1e-6), (854, 480, "haze", 0.01),
+                                           (1023, 37, "levels", 0.3)])
+def test_airlight_selection_bit_exact(W, H, kind, frac):
+    I = _img(W, H, 5, kind)
+    with context(top_fraction=frac) as (m, ctx):
+        info = m.hz_estimate_airlight(ctx, to_dev(I, 5))
+    prm = oracle_params(top_fraction=frac)
+    D = O.dark_channel(I, 15)
+    al = O.airlight(I, D, prm.top_fraction, prm.alpha)
+    assert info.K == al["K"]
+    assert info.T == al["T"]
+    assert info.n_above == al["n_above"]
+    assert info.cut_index == al["cut_index"]
+    assert list(info.S) == [int(v) for v in al["S"]]
+    np.testing.assert_allclose(np.array(info.A_hat, dtype=np.float64), al["A_hat"], rtol=2.5e-7, atol=0)
+
+
+def test_airlight_constant_image_all_ties():
+    I = np.empty((97, 131, 3), np.uint8)
+    I[:] = (90, 200, 150)
+    with context(top_fraction=0.01) as (m, ctx):
+        info = m.hz_estimate_airlight(ctx, to_dev(I))
+    K = O.num_top(97 * 131, 0.01)
+    assert info.T == 90 and info.n_above == 0 and info.cut_index == K - 1
+    assert list(info.S) == [90 * K, 200 * K, 150 * K]
+
+
+@pytest.mark.parametrize("mode", ["dcp", "fast"])
+@pytest.mark.parametrize("W,H", [(200, 150), (854, 480), (1023, 37)])
+def test_transmission_within_1e6(mode, W, H):
+    I = _img(W, H, 9, "haze")
+    A = [0.81, 0.86, 0.9]
+    kw = dict(t_mode=mode, omega=0.95 if mode == "dcp" else 0.5, t0=0.1 if mode == "dcp" else 0.05)
+    with context(**kw) as (m, ctx):
+        t = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+        m.hz_transmission(ctx, to_dev(I, 3), A, t)
+        tg = t.cpu().numpy().astype(np.float64)
+    prm = oracle_params(**kw)
+    Af = np.array(A, dtype=np.float32).astype(np.float64)
+    if mode == "dcp":
+        tr = O.transmission_dcp(I, Af, prm.omega, prm.t0, prm.patch)
+    else:
+        tr = O.transmission_fast(I, Af, prm.omega, prm.t0)
+    assert np.abs(tg - tr).max() <= 1e-6
+    assert tg.min() >= prm.t0 - 1e-7 and tg.max() <= 1.0
+
+
+@pytest.mark.parametrize("balance", [0, 1])
+@pytest.mark.parametrize("gamma", [1.0, 1.2, 2.2])
+def test_recover_within_1lsb(balance, gamma):
+    W, H = 333, 201
+    I = _img(W, H, 11, "haze")
+    g = np.random.default_rng(1)
+    t = g.uniform(0.1, 1.0, size=(H, W)).astype(np.float32)
+    A = [0.8, 0.84, 0.88]
+    with context(gamma=gamma, color_balance=balance) as (m, ctx):
+        out, _ = empty_dev(W, H, 7)
+        info = m.hz_recover(ctx, to_dev(I, 1), torch.from_numpy(t).cuda(), A, out, want_info=True)
+        o = out.cpu().numpy()
+    prm = oracle_params(gamma=gamma)
+    J = O.recover(I, t.astype(np.float64), np.array(A, np.float32).astype(np.float64))
+    Jg = O.gamma_correct(J, prm.gamma)
+    if balance:
+        y, gains, mu = O.gray_world(Jg)
+        np.testing.assert_allclose(np.array(info.gains), gains, rtol=1e-5)
+    else:
+        y = Jg
+        assert list(info.gains) == [1.0, 1.0, 1.0]
+    mx, exact = u8_diff(o, O.quantize(y))
+    assert mx <= 1 and exact > 0.99
+
+
+CONFIGS = [
+    dict(),
+    dict(color_balance=1),
+    dict(t_mode="fast", omega=0.5, t0=0.05),
+    dict(patch=3, gamma=1.0),
+    dict(patch=31, top_fraction=0.01, alpha=1.0),
+]
+
+
+@pytest.mark.parametrize("kw", CONFIGS)
+@pytest.mark.parametrize("W,H,pad", [(640, 480, 0), (201, 133, 5), (854, 480, 2)])
+def test_frame_within_1lsb(kw, W, H, pad):
+    I = hazegen.make_frame(W, H, seed=W + H, beta=1.0)
+    with context(**kw) as (m, ctx):
+        out, buf = empty_dev(W, H, pad, fill=0xAB)
+        info = m.hz_dehaze_frame(ctx, to_dev(I, pad), out, want_info=True)
+        o = out.cpu().numpy()
+        b = buf.cpu().numpy()
+    ref = O.dehaze_frame(I, oracle_params(**kw))
+    assert info.T == ref.T and info.cut_index == ref.cut_index
+    assert list(info.S) == [int(v) for v in ref.S]
+    np.testing.assert_allclose(np.array(info.A, np.float64), ref.A, rtol=3e-7)
+    mx, exact = u8_diff(o, ref.out)
+    assert mx <= 1, mx
+    assert exact > 0.995, exact
+    if pad:  # bytes between rows are untouched
+        pitch = 3 * W + pad
+        for y in range(H - 1):
+            assert np.all(b[y * pitch + 3 * W:(y + 1) * pitch] == 0xAB)
+    assert np.all(b[(H - 1) * (3 * W + pad) + 3 * W:] == 0xAB)
+
+
+def test_identity_when_omega0_gamma1():
+    W, H = 300, 200
+    I = hazegen.make_frame(W, H, seed=4)
+    with context(omega=0.0, gamma=1.0) as (m, ctx):
+        out, _ = empty_dev(W, H)
+        m.hz_dehaze_frame(ctx, to_dev(I), out)
+        np.testing.assert_array_equal(out.cpu().numpy(), I)
+
+
+def test_I_equals_A_gives_A():
+    W, H = 150, 100
+    I = np.empty((H, W, 3), np.uint8)
+    I[:] = (204, 153, 230)
+    A = tuple(float(np.float32(v / 255)) for v in I[0, 0])
+    with context(airlight_override=A, gamma=1.0) as (m, ctx):
+        out, _ = empty_dev(W, H)
+        m.hz_dehaze_frame(ctx, to_dev(I), out)
+        np.testing.assert_array_equal(out.cpu().numpy(), I)
+
+
+def test_video_sequence_ema_matches_oracle():
+    W, H, F = 320, 240, 7
+    frames = hazegen.make_sequence(W, H, F, seed=2, period=F)
+    kw = dict(airlight_ema=0.9)
+    with context(**kw) as (m, ctx):
+        inp = torch.from_numpy(frames).cuda()
+        out = torch.empty_like(inp)
+        infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
+        o = out.cpu().numpy()
+    ref = O.dehaze_sequence(list(frames), oracle_params(**kw))
+    for f in range(F):
+        assert infos[f].T == ref[f].T and infos[f].cut_index == ref[f].cut_index
+        np.testing.assert_allclose(np.array(infos[f].A, np.float64), ref[f].A, rtol=3e-7)
+        mx, exact = u8_diff(o[f], ref[f].out)
+        assert mx <= 1 and exact > 0.995
+
+
+def test_video_stream_state_carries_across_calls():
+    W, H, F = 160, 120, 6
+    frames = hazegen.make_sequence(W, H, F, seed=3, period=F)
+    with context(airlight_ema=0.9) as (m, ctx):
+        inp = torch.from_numpy(frames).cuda()
+        out_all = torch.empty_like(inp)
+        ia = m.hz_dehaze_video(ctx, inp, out_all, want_info=True)
+        sid = m.hz_open_stream(ctx, W, H)
+        out_split = torch.empty_like(inp)
+        ib = m.hz_dehaze_video(ctx, inp[:2], out_split[:2], stream_id=sid, want_info=True)
+        state = m.hz_stream_get_state(ctx, sid)
+        m.hz_close_stream(ctx, sid)
+        sid2 = m.hz_open_stream(ctx, W, H)
+        m.hz_stream_set_state(ctx, sid2, state)
+        ic = m.hz_dehaze_video(ctx, inp[2:], out_split[2:], stream_id=sid2, want_info=True)
+        for f in range(F):
+            i2 = ib[f] if f < 2 else ic[f - 2]
+            assert list(ia[f].A) == list(i2.A)
+        assert torch.equal(out_all, out_split)
+
+
+def test_video_host_io_matches_device_path():
+    W, H, F = 256, 144, 9
+    frames = hazegen.make_sequence(W, H, F, seed=5, period=F)
+    with context(airlight_ema=0.9) as (m, ctx):
+        dev_in = torch.from_numpy(frames).cuda()
+        dev_out = torch.empty_like(dev_in)
+        m.hz_dehaze_video(ctx, dev_in, dev_out)
+        h_in = torch.from_numpy(frames).pin_memory()
+        h_out = torch.zeros_like(h_in).pin_memory()
+        m.hz_dehaze_video(ctx, h_in, h_out, flags=m.HZ_IO_HOST)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out, dev_out.cpu())
+
+
+def test_batch_mixed_sizes_matches_single_frames():
+    specs = [(854, 480, 1), (1280, 720, 2), (320, 200, 3), (1023, 37, 4), (64, 64, 5)]
+    frames = [hazegen.make_frame(W, H, seed=s) for (W, H, s) in specs]
+    with context() as (m, ctx):
+        ins = [to_dev(I, 3) for I in frames]
+        outs = [empty_dev(W, H, 1)[0] for (W, H, _) in specs]
+        infos = m.hz_dehaze_batch(ctx, ins, outs, want_info=True)
+        for k, I in enumerate(frames):
+            single, _ = empty_dev(specs[k][0], specs[k][1])
+            m.hz_dehaze_frame(ctx, ins[k], single)
+            assert torch.equal(single, outs[k])
+        for k in (0, 3, 4):
+            ref = O.dehaze_frame(frames[k], oracle_params())
+            assert infos[k].T == ref.T and infos[k].cut_index == ref.cut_index
+            mx, _ = u8_diff(outs[k].cpu().numpy(), ref.out)
+            assert mx <= 1
+
+
+def test_bad_arguments_are_rejected():
+    with context() as (m, ctx):
+        I = to_dev(hazegen.make_frame(32, 32, seed=1))
+        out, _ = empty_dev(32, 32)
+        with pytest.raises(m.HzError) as e:
+            m.hz_dehaze_frame(ctx, I, out, stream_id=5)
+        assert e.value.status == m.HZ_ESTATE
+        lib = m.binding.lib()
+        assert lib.hz_dehaze_frame(ctx, -1, I.data_ptr(), 32, 32, 10, out.data_ptr(), 96, None, None) == m.HZ_EINVAL
+        assert lib.hz_dehaze_frame(ctx, -1, I.data_ptr(), 0, 32, 96, out.data_ptr(), 96, None, None) == m.HZ_EINVAL
+        assert lib.hz_dehaze_frame(ctx, -1, None, 32, 32, 96, out.data_ptr(), 96, None, None) == m.HZ_EINVAL
+        assert "pitch" in m.hz_last_error(ctx) or "NULL" in m.hz_last_error(ctx)
+
+
+def test_full_size_1080p_frame():
+    """The 1920x1080 workload frame in the bench's launch configuration."""
+    I = hazegen.make_frame(1920, 1080, seed=2, beta=1.0)
+    with context(airlight_ema=0.9) as (m, ctx):
+        inp = torch.from_numpy(I[None]).cuda()
+        out = torch.empty_like(inp)
+        infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
+        o = out[0].cpu().numpy()
+    ref = O.dehaze_frame(I, oracle_params(airlight_ema=0.9))
+    assert infos[0].T == ref.T and infos[0].cut_index == ref.cut_index
+    assert list(infos[0].S) == [int(v) for v in ref.S]
+    mx, exact = u8_diff(o, ref.out)
+    assert mx <= 1 and exact > 0.995
