@@ -32,11 +32,16 @@ sys.path.insert(0, ROOT)
 
 import hazegen  # noqa: E402
 
-W, H, F = 1920, 1080, 300
+W, H = 1920, 1080
+F = 300  # frames per step (--frames changes it for profiling runs only)
 SEED = 2
 METRIC = "1080p frames/s"
 WORKLOAD = "video 300x1920x1080 RGB u8, patch 15, omega 0.95, t0 0.1, top 0.001, EMA 0.9"
 ALG_BYTES_PER_PX = 6.0  # read I once, write the output once
+# algorithmic bytes per pixel of each kernel class: what its inputs and
+# outputs must move once (dark: I in, P out; recon: I and P in, out written;
+# fused: the whole path, I in and out written)
+KERNEL_BYTES_PER_PX = {"dark": 6.0, "recon": 9.0, "fused": 6.0, "select": 0.0, "airlight": 0.0}
 
 
 def _render_range(args):
@@ -49,6 +54,7 @@ def make_inputs(nproc):
     """The 300-frame sequence, rendered in a spawn pool (started before any
     CUDA call)."""
     chunks = [(i, min(F, i + 10)) for i in range(0, F, 10)]
+    nproc = min(nproc, len(chunks))
     out = np.empty((F, H, W, 3), np.uint8)
     if nproc > 1:
         ctx = mp.get_context("spawn")
@@ -178,8 +184,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-out", default="")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames", type=int, default=300,
+                    help="frames per step; only profiling runs change it from the 300-frame workload")
     args = ap.parse_args()
+    global F
+    F = args.frames
     if args.impl == "reference":
         return run_reference(args)
 
@@ -249,7 +259,7 @@ def main():
     top = max(kprof, key=lambda k: kprof[k]["ms"])
     peak, peak_kind = load_peaks()
     px_step = F * W * H
-    kbytes = {"dark": 6.0, "recon": 9.0, "select": 0.0, "airlight": 0.0}
+    kbytes = KERNEL_BYTES_PER_PX
     launches_top = max(kprof[top]["timed"], 1)
     avg_ms = kprof[top]["ms"] / launches_top
     px_launch = px_step * args.steps / launches_top
@@ -265,9 +275,32 @@ def main():
             traffic = None
 
     # ---- e2e: same call with pinned host buffers (copies in the region) ---
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(hzp, ctx, frames_np, out, dev, args.steps, ws, barrier)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n_sample = 8
+        v, dt = cpu_baseline(frames_np, n_sample)
+        cpu = {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_sample} frames of the sequence, FP64 NumPy oracle, {dt:.1f} s"}
+
+    hzp.hz_destroy(ctx)
+    if rank == 0:
+        emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
+             launches, clocks)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
+    import torch
     h_in = torch.from_numpy(frames_np).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(steps, 5))
     hzp.hz_dehaze_video(ctx, h_in, h_out, flags=hzp.HZ_IO_HOST)
     torch.cuda.synchronize()
     barrier()
@@ -279,16 +312,13 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = ws * F * e2e_steps / e2e_s
     ok = torch.equal(h_out.to(dev), out)
+    return {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": F * W * H * 3,
+            "d2h_bytes_per_step": F * W * H * 3, "matches_device_path": bool(ok)}
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        n_sample = 8
-        v, dt = cpu_baseline(frames_np, n_sample)
-        cpu = {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_sample} frames of the sequence, FP64 NumPy oracle, {dt:.1f} s"}
 
-    hzp.hz_destroy(ctx)
-    if rank == 0:
+def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
+         launches, clocks):
+    if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True,
@@ -301,19 +331,15 @@ def main():
                               "frac_of_measured": value * W * H * ALG_BYTES_PER_PX / 1e9 / peak},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "alg_bytes_per_px": kbytes.get(top, ALG_BYTES_PER_PX), "avg_launch_ms": avg_ms},
+                         "alg_bytes_per_px": KERNEL_BYTES_PER_PX.get(top, ALG_BYTES_PER_PX),
+                         "avg_launch_ms": avg_ms},
             "kernels": {k: v for k, v in kprof.items() if v["launches"]},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": F * W * H * 3,
-                    "d2h_bytes_per_step": F * W * H * 3, "matches_device_path": bool(ok)},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":
