@@ -282,6 +282,31 @@ hz_status hz_set_profiling(hz_ctx* ctx, int on);
  * copy them to *out and, if reset != 0, clear them. */
 hz_status hz_get_profile(hz_ctx* ctx, hz_profile* out, int reset);
 
+/* --------------------------------------------- allocation-free frame -- */
+/* The paper has no counterpart to this call; it exists for callers that are
+ * not allowed to allocate device memory at run time: plug-ins that run inside
+ * a host application which owns the GPU's memory budget, real-time camera
+ * loops where cudaMalloc could stall the frame (it may synchronise the
+ * device), and deployments whose rules forbid dynamic allocation after start-up.
+ *
+ * It dehazes one frame in video mode like hz_dehaze_frame with stream_id -1
+ * (no smoothing across frames, no hz_ctx needed), and allocates nothing: its
+ * scratch is a static 2 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits. Frames whose scratch
+ * does not fit are rejected with HZ_EINVAL; 854x480 and smaller fit (so does
+ * 640x480, the paper's default processing size), 1280x720 does not.
+ *  - p: parameters (as for hz_create); in/out: device pointers, layout as for
+ *    every other call; cuda_stream: the stream to enqueue on.
+ *  - The first call on a device looks up the array's device address and sets
+ *    kernel attributes; make that first call before any stream capture.
+ *  - Every call shares the one array and clears the parts that must start at
+ *    zero, so calls whose work overlaps on the GPU (different streams, or
+ *    host threads) race and corrupt each other: order them on one stream.
+ *  - err (optional, err_len bytes) receives a message on failure. */
+hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* in, int32_t W, int32_t H,
+                                  size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
+                                  char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -139,6 +139,7 @@ _SIGS = {
     "hz_stream_get_state": (C.c_int, [_P, _I, _P, _SZ]),
     "hz_stream_set_state": (C.c_int, [_P, _I, _P, _SZ]),
     "hz_get_server_stats": (C.c_int, [_P, C.POINTER(hz_server_stats)]),
+    "hz_dehaze_frame_noalloc": (C.c_int, [C.POINTER(hz_params), _P, _I, _I, _SZ, _P, _SZ, _P, C.c_char_p, _SZ]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
     "hz_get_profile": (C.c_int, [_P, C.POINTER(hz_profile), C.c_int]),
 }
@@ -420,3 +421,14 @@ def hz_get_profile(ctx, reset: bool = False) -> dict:
     _check(lib().hz_get_profile(ctx, C.byref(p), 1 if reset else 0), ctx, "hz_get_profile")
     return {HZ_K_NAMES[k]: {"launches": int(p.launches[k]), "timed": int(p.timed[k]), "ms": float(p.ms[k])}
             for k in range(HZ_K_COUNT)}
+
+
+def hz_dehaze_frame_noalloc(p: hz_params, inp, out, stream=None):
+    """The allocation-free single-frame call (static library scratch)."""
+    pi, W, H, ip = frame_args(inp)
+    po, _, _, op = frame_args(out)
+    err = C.create_string_buffer(256)
+    st = lib().hz_dehaze_frame_noalloc(C.byref(p), pi, W, H, ip, po, op, _stream_ptr(stream), err, 256)
+    if st != HZ_OK:
+        raise HzError(st, f"hz_dehaze_frame_noalloc: {hz_status_str(st)}: {err.value.decode()}")
+    return st

@@ -855,3 +855,152 @@ extern "C" hz_status hz_get_profile(hz_ctx* c, hz_profile* out, int reset) {
   }
   return HZ_OK;
 }
+
+// ------------------------------------------- allocation-free frame call --
+// For callers that must not allocate device memory: the scratch of one
+// video-mode frame lives in this file-scope array instead of a context's
+// arena. Host code may not use the array's name as a device address; the
+// address is looked up once per device with cudaGetSymbolAddress.
+
+namespace hz {
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(2) << 20;  // 2 MiB per device
+}  // namespace hz
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[hz::NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+void noalloc_msg(char* err, size_t len, const char* fmt, ...) {
+  if (!err || len == 0) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(err, len, fmt, ap);
+  va_end(ap);
+}
+
+// Once per device, with that device current: the array's device address and
+// the dark-channel kernels' shared-memory attribute.
+hz_status noalloc_setup(int dev, void** out, char* err, size_t len) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (dev < 0 || dev >= kMaxDevices) {
+    noalloc_msg(err, len, "device %d out of range", dev);
+    return HZ_EINVAL;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      noalloc_msg(err, len, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return HZ_ECUDA;
+    }
+    cudaError_t a = cudaSuccess;
+#define HZ_NA_ATTR(r) if (a == cudaSuccess) a = set_attr_one<r>();
+    HZ_NA_ATTR(0) HZ_NA_ATTR(1) HZ_NA_ATTR(2) HZ_NA_ATTR(3) HZ_NA_ATTR(4) HZ_NA_ATTR(5) HZ_NA_ATTR(6)
+    HZ_NA_ATTR(7) HZ_NA_ATTR(8) HZ_NA_ATTR(9) HZ_NA_ATTR(10) HZ_NA_ATTR(11) HZ_NA_ATTR(12) HZ_NA_ATTR(13)
+    HZ_NA_ATTR(14) HZ_NA_ATTR(15)
+#undef HZ_NA_ATTR
+    if (a != cudaSuccess) {
+      noalloc_msg(err, len, "cudaFuncSetAttribute: %s", cudaGetErrorString(a));
+      return HZ_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return HZ_OK;
+}
+
+}  // namespace
+
+extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* in, int32_t W, int32_t H,
+                                             size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
+                                             char* err, size_t err_len) {
+  if (validate(nullptr, p) != HZ_OK) {
+    noalloc_msg(err, err_len, "invalid parameters");
+    return HZ_EINVAL;
+  }
+  if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || !in || !out || in_pitch < size_t(3) * W ||
+      out_pitch < size_t(3) * W) {
+    noalloc_msg(err, err_len, "bad frame arguments (%dx%d)", W, H);
+    return HZ_EINVAL;
+  }
+  const bool bal = p->color_balance != 0;
+  LaunchPlan lp;
+  plan_frames(*p, &W, &H, 1, false, bal, lp);
+  if (lp.total > NOALLOC_SCRATCH_BYTES) {
+    noalloc_msg(err, err_len, "a %dx%d frame needs %zu bytes of scratch; the static scratch holds %zu", W, H,
+                lp.total, NOALLOC_SCRATCH_BYTES);
+    return HZ_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    noalloc_msg(err, err_len, "no current CUDA device");
+    return HZ_ECUDA;
+  }
+  void* base_v = nullptr;
+  hz_status st = noalloc_setup(dev, &base_v, err, err_len);
+  if (st != HZ_OK) return st;
+  uint8_t* base = static_cast<uint8_t*>(base_v);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  HzJobs jobs;
+  jobs.n = 1;
+  HzJob& j = jobs.j[0];
+  const FramePlan& f = lp.fp[0];
+  j = HzJob{};
+  j.in = in;
+  j.out = out;
+  j.in_pitch = (long long)in_pitch;
+  j.out_pitch = (long long)out_pitch;
+  j.W = W;
+  j.H = H;
+  j.tiles_x = f.tiles_x;
+  j.tiles_y = f.tiles_y;
+  j.segs = f.segs;
+  j.tsrc = (p->t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  j.K = f.K;
+  j.P = base + f.off_P;
+  j.P_pitch = f.P_pitch;
+  j.tilemax = base + f.off_tilemax;
+  j.rowcnt = reinterpret_cast<unsigned*>(base + f.off_rowcnt);
+  j.rowsum = reinterpret_cast<unsigned*>(base + f.off_rowsum);
+  j.rec = reinterpret_cast<HzFrameRec*>(base + f.off_rec);
+  j.bal_part = f.off_bal ? reinterpret_cast<double*>(base + f.off_bal) : nullptr;
+  j.state = nullptr;
+  j.use_override = p->use_airlight_override;
+  const HzKParams kp = kparams_of(*p);
+
+  // the counters, histogram and per-row sums of the previous call must not
+  // leak into this one
+  cudaError_t e = cudaMemsetAsync(base, 0, lp.zero_bytes, s);
+  const dim3 g1(f.tiles_x * f.tiles_y, 1);
+  const dim3 g3(H * f.segs, 1);
+  if (e == cudaSuccess) {
+    switch (p->patch / 2) {
+#define HZ_NA_P1(r) \
+  case r: k_p1<r><<<g1, P1_THREADS, P1G<r>::SMEM, s>>>(jobs); break;
+      HZ_NA_P1(0) HZ_NA_P1(1) HZ_NA_P1(2) HZ_NA_P1(3) HZ_NA_P1(4) HZ_NA_P1(5) HZ_NA_P1(6) HZ_NA_P1(7)
+      HZ_NA_P1(8) HZ_NA_P1(9) HZ_NA_P1(10) HZ_NA_P1(11) HZ_NA_P1(12) HZ_NA_P1(13) HZ_NA_P1(14) HZ_NA_P1(15)
+#undef HZ_NA_P1
+      default: break;
+    }
+    k_p2<<<g1, 256, 0, s>>>(jobs, kp);
+    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+    if (bal) {
+      k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+      k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+    } else {
+      k_p3<M_OUT><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+    }
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    noalloc_msg(err, err_len, "launch failed: %s", cudaGetErrorString(e));
+    return HZ_ECUDA;
+  }
+  return HZ_OK;
+}
