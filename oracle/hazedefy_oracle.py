@@ -38,6 +38,8 @@ Readings of points the paper leaves open (each is a parameter here):
       A_0 = Ahat_0; lam = 0 disables it.
 * C10 quantisation: out = rint(255 * x), half to even.
 * C11 order: gamma, then balance, then quantise; no resize.
+* C12 inside the ratio I^c / A^c a channel of A below 1e-6 is floored at
+      1e-6 (only reachable when the selected pixels are black in a channel).
 
 Parity status: every function here is pinned by tests against closed forms,
 brute force, invariants or hand-worked fixtures, except the colour balance,
@@ -52,6 +54,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 GRAY_WEIGHTS = (0.299, 0.587, 0.114)
+A_FLOOR = 1e-6  # reading C12
 
 
 @dataclass
@@ -171,7 +174,7 @@ def ema_airlight(A_hats, lam: float) -> np.ndarray:
 def transmission_dcp(I: np.ndarray, A, omega: float, t0: float, patch: int) -> np.ndarray:
     """t = max(1 - omega * min_{y in Omega(x)} min_c I_n^c(y) / A^c, t0)
     (the patch form of the transmission, reading C1, with the Eq. 5 clamp)."""
-    A = np.asarray(A, dtype=np.float64)
+    A = np.maximum(np.asarray(A, dtype=np.float64), A_FLOOR)
     In = I.astype(np.float64) / 255.0
     m = (In / A[None, None, :]).min(axis=2)
     return np.maximum(1.0 - omega * patch_min(m, patch), t0)
@@ -179,7 +182,7 @@ def transmission_dcp(I: np.ndarray, A, omega: float, t0: float, patch: int) -> n
 
 def transmission_fast(I: np.ndarray, A, omega: float, t0: float) -> np.ndarray:
     """Eq. 4: that(x) = 1 - omega * min_c I_n^c(x) / max(A); Eq. 5 clamp."""
-    A = np.asarray(A, dtype=np.float64)
+    A = np.maximum(np.asarray(A, dtype=np.float64), A_FLOOR)
     In = I.astype(np.float64) / 255.0
     that = 1.0 - omega * In.min(axis=2) / A.max()
     return np.maximum(that, t0)
