@@ -370,9 +370,8 @@ def test_params_f32_rounding():
 def test_transmission_black_airlight_channel_is_finite():
     """Reading C12: a zero airlight channel is floored inside I/A, so t stays
     finite and the zero channel (whose ratio is huge) never wins the min."""
-    I = np.zeros((8, 9, 3), np.uint8)
-    I[:, :, 0] = 40
-    t = O.transmission_dcp(I, [0.5, 0.0, 0.0], 0.95, 0.1, 3)
+    I = np.empty((8, 9, 3), np.uint8)
+    I[:] = (40, 30, 20)
+    t = O.transmission_dcp(I, [0.5, 0.0, 0.4], 0.95, 0.1, 3)
     assert np.all(np.isfinite(t))
-    np.testing.assert_allclose(t, 1 - 0.95 * (40 / 255) / 0.5 * 0 - 0.95 * 0, atol=1)  # finite, in range
-    assert t.min() >= 0.1 and t.max() <= 1.0
+    np.testing.assert_allclose(t, 1 - 0.95 * (20 / 255) / 0.4, rtol=1e-15)
