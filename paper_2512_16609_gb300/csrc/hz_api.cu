@@ -133,7 +133,7 @@ static int max_tiles(const HzJobs& jobs) {
 
 static int max_units(const HzJobs& jobs) {
   int m = 1;
-  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].H * jobs.j[i].segs);
+  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].segs);
   return m;
 }
 
@@ -151,7 +151,7 @@ static hz_status run_front(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, cudaSt
   HZ_CK(c, cudaGetLastError());
   {
     LaunchScope ls(c, HZ_K_AIRLIGHT, s);
-    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+    k_fin<<<1, FIN_THREADS, 0, s>>>(jobs, kp);
   }
   HZ_CK(c, cudaGetLastError());
   return HZ_OK;
@@ -723,7 +723,7 @@ static hz_status stage_with_A(hz_ctx* c, const uint8_t* in, int W, int H, size_t
   }
   {
     LaunchScope ls(c, HZ_K_AIRLIGHT, s);
-    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+    k_fin<<<1, FIN_THREADS, 0, s>>>(jobs, kp);
   }
   HZ_CK(c, cudaGetLastError());
   return HZ_OK;
@@ -747,7 +747,7 @@ extern "C" hz_status hz_transmission(hz_ctx* c, const uint8_t* in, int32_t W, in
   const HzKParams kp = kparams_of(c->prm);
   {
     LaunchScope ls(c, HZ_K_TRANS, s);
-    k_p3<M_T_ONLY><<<dim3(H * jobs.j[0].segs, 1), P3_THREADS, 0, s>>>(jobs, kp);
+    k_p3<M_T_ONLY><<<dim3(jobs.j[0].segs, 1), P3_THREADS, 0, s>>>(jobs, kp);
   }
   HZ_CK(c, cudaGetLastError());
   return mark_done(c, s);
@@ -978,7 +978,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   // leak into this one
   cudaError_t e = cudaMemsetAsync(base, 0, lp.zero_bytes, s);
   const dim3 g1(f.tiles_x * f.tiles_y, 1);
-  const dim3 g3(H * f.segs, 1);
+  const dim3 g3(f.segs, 1);
   if (e == cudaSuccess) {
     switch (p->patch / 2) {
 #define HZ_NA_P1(r) \
@@ -989,7 +989,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
       default: break;
     }
     k_p2<<<g1, 256, 0, s>>>(jobs, kp);
-    k_fin<<<1, 32, 0, s>>>(jobs, kp);
+    k_fin<<<1, FIN_THREADS, 0, s>>>(jobs, kp);
     if (bal) {
       k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
       k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);

@@ -24,8 +24,12 @@ constexpr int P1_TH = 32;       // tile height in rows
 constexpr int P1_THREADS = 256;
 // ---- pointwise reconstruction kernels ----------------------------------
 constexpr int P3_THREADS = 256;
-constexpr int P3_PX = 4;                        // pixels per thread
-constexpr int P3_SEG = P3_THREADS * P3_PX;      // pixels per block and row
+constexpr int P3_GPX = 16;                      // pixels per thread (48 bytes of I)
+// reconstruction blocks of a W x H frame
+inline __host__ __device__ int p3_units(int W, int H) {
+  const long long groups = (long long)((W + P3_GPX - 1) / P3_GPX) * H;
+  return int((groups + P3_THREADS - 1) / P3_THREADS);
+}
 // ---- guided filter ------------------------------------------------------
 constexpr int GF_VBAND = 64;    // output rows per vertical-pass block
 constexpr int GF_VCOLS = 128;   // columns per vertical-pass block
@@ -77,7 +81,7 @@ struct HzJob {
   long long in_pitch, out_pitch;
   int W, H;
   int tiles_x, tiles_y;         // dark-channel tiling
-  int segs;                     // reconstruction segments per row
+  int segs;                     // reconstruction blocks of the frame (p3_units)
   int tsrc;                     // TSource for the reconstruction pass
   long long K;
   uint8_t* P;

@@ -503,31 +503,68 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
 }
 
 // ------------------------------------------------------------------------
-// Airlight finish, frames in launch order (one thread): override or
-// smoothing A_f = lam A_{f-1} + (1 - lam) A_hat_f through the frame's state.
-__global__ void k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int f = 0; f < jobs.n; ++f) {
-    const HzJob& jb = jobs.j[f];
-    HzFrameRec* rec = jb.rec;
-    double A[3];
-    if (jb.use_override) {
-      for (int c = 0; c < 3; ++c) A[c] = double(kp.ov[c]);
-    } else if (jb.state && kp.ema > 0.f && jb.state->frames > 0) {
-      const double lam = double(kp.ema);
-      for (int c = 0; c < 3; ++c) A[c] = lam * jb.state->A[c] + (1.0 - lam) * rec->A_hat[c];
-    } else {
-      for (int c = 0; c < 3; ++c) A[c] = rec->A_hat[c];
+// Airlight finish, frames in launch order: override, or smoothing
+// A_f = lam A_{f-1} + (1 - lam) A_hat_f through each frame's stream state.
+// Loads and stores are spread over the block; the chain itself runs in one
+// thread on shared memory.
+constexpr int FIN_THREADS = 64;
+__global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+  __shared__ double sAh[MAXJ][3];
+  __shared__ double sA[MAXJ][3];
+  __shared__ HzStreamState* sptr[MAXJ];
+  __shared__ double sst[MAXJ][3];
+  __shared__ long long sfr[MAXJ];
+  const int n = jobs.n, tid = threadIdx.x;
+  for (int f = tid; f < n; f += FIN_THREADS) {
+    const HzFrameRec* rec = jobs.j[f].rec;
+    sAh[f][0] = rec->A_hat[0];
+    sAh[f][1] = rec->A_hat[1];
+    sAh[f][2] = rec->A_hat[2];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int nst = 0;
+    const double lam = double(kp.ema);
+    for (int f = 0; f < n; ++f) {
+      const HzJob& jb = jobs.j[f];
+      double A[3];
+      if (jb.use_override) {
+        for (int c = 0; c < 3; ++c) A[c] = double(kp.ov[c]);
+      } else if (jb.state) {
+        int k = 0;
+        while (k < nst && sptr[k] != jb.state) ++k;
+        if (k == nst) {
+          sptr[k] = jb.state;
+          for (int c = 0; c < 3; ++c) sst[k][c] = jb.state->A[c];
+          sfr[k] = jb.state->frames;
+          ++nst;
+        }
+        if (kp.ema > 0.f && sfr[k] > 0) {
+          for (int c = 0; c < 3; ++c) A[c] = lam * sst[k][c] + (1.0 - lam) * sAh[f][c];
+        } else {
+          for (int c = 0; c < 3; ++c) A[c] = sAh[f][c];
+        }
+        for (int c = 0; c < 3; ++c) sst[k][c] = A[c];
+        sfr[k] += 1;
+      } else {
+        for (int c = 0; c < 3; ++c) A[c] = sAh[f][c];
+      }
+      for (int c = 0; c < 3; ++c) sA[f][c] = A[c];
     }
-    if (jb.state && !jb.use_override) {
-      for (int c = 0; c < 3; ++c) jb.state->A[c] = A[c];
-      jb.state->frames += 1;
+    for (int k = 0; k < nst; ++k) {
+      for (int c = 0; c < 3; ++c) sptr[k]->A[c] = sst[k][c];
+      sptr[k]->frames = sfr[k];
     }
+  }
+  __syncthreads();
+  for (int f = tid; f < n; f += FIN_THREADS) {
+    HzFrameRec* rec = jobs.j[f].rec;
     double amax = 0.0;
     for (int c = 0; c < 3; ++c) {
-      rec->A_used[c] = A[c];
-      rec->A[c] = float(A[c]);
-      const double af = fmax(double(float(A[c])), double(A_FLOOR));
+      const double a = sA[f][c];
+      rec->A_used[c] = a;
+      rec->A[c] = float(a);
+      const double af = fmax(double(float(a)), double(A_FLOOR));
       rec->inv[c] = float(1.0 / (255.0 * af));
       amax = fmax(amax, af);
     }
@@ -536,131 +573,194 @@ __global__ void k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
 }
 
 // ------------------------------------------------------------------------
-// p3: pointwise reconstruction of 4 pixels per thread.
-__device__ __forceinline__ void load12(const uint8_t* p, bool aligned, int nv, uint32_t (&w)[3]) {
-  if (aligned && nv == 4) {
-    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
-    w[0] = __ldcs(q); w[1] = __ldcs(q + 1); w[2] = __ldcs(q + 2);
-  } else {
-    uint8_t b[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) b[i] = (i < 3 * nv) ? p[i] : 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      w[k] = uint32_t(b[4 * k]) | (uint32_t(b[4 * k + 1]) << 8) | (uint32_t(b[4 * k + 2]) << 16) |
-             (uint32_t(b[4 * k + 3]) << 24);
-  }
+// p3: pointwise reconstruction, 16 pixels per thread.
+//
+// Conversions stay off the XU pipe: a byte v becomes the float 2^23 + v by
+// one PRMT into 0x4B000000, and fma(2^23 + v, c, -2^23 c) = fl(v c) exactly
+// (2^23 c is exact, the FMA rounds once); rint(255 x) for x in [0, 1] is the
+// low byte of fma(x, 255, 1.5 2^23) (round to nearest even in the FMA).
+// Gamma uses the hardware base-2 logarithm / exponential approximations,
+// 1/t the hardware reciprocal approximation.
+
+__device__ __forceinline__ float bytef(uint32_t w, int k) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u | uint32_t(k)));
+}
+__device__ __forceinline__ float ex2a(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2a(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcpa(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float TWO23 = 8388608.f;
+constexpr float MAGIC_RINT = 12582912.f;  // 1.5 * 2^23
+constexpr float INV255 = 1.f / 255.f;
+
+__device__ __forceinline__ uint32_t pack4(float a, float b, float c, float d) {
+  const uint32_t lo = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x0040u);
+  const uint32_t hi = __byte_perm(__float_as_uint(c), __float_as_uint(d), 0x0040u);
+  return __byte_perm(lo, hi, 0x5410u);
 }
 
-__device__ __forceinline__ void store12(uint8_t* p, bool aligned, int nv, const uint32_t (&w)[3]) {
-  if (aligned && nv == 4) {
-    uint32_t* q = reinterpret_cast<uint32_t*>(p);
-    __stcs(q, w[0]); __stcs(q + 1, w[1]); __stcs(q + 2, w[2]);
-  } else {
-    for (int i = 0; i < 3 * nv; ++i) p[i] = uint8_t((w[i >> 2] >> (8 * (i & 3))) & 0xff);
-  }
-}
-
-__device__ __forceinline__ unsigned byte_of(const uint32_t (&w)[3], int i) {
+__device__ __forceinline__ unsigned byte_of(const uint32_t* w, int i) {
   return (w[i >> 2] >> (8 * (i & 3))) & 0xffu;
+}
+
+struct P3Const {
+  float A[3], inv[3], ninv[3], inv_fast, ninv_fast, gains[3];
+};
+
+// t of pixel k of a group (bytes of I in iw, of P in pw; plane pointer tp)
+__device__ __forceinline__ float t_of(int tsrc, const uint32_t* iw, const uint32_t* pw, const void* tp, int k,
+                                      const P3Const& K, const HzKParams& kp) {
+  if (tsrc == TS_P) {
+    const float m0 = fmaf(bytef(pw[(3 * k) >> 2], (3 * k) & 3), K.inv[0], K.ninv[0]);
+    const float m1 = fmaf(bytef(pw[(3 * k + 1) >> 2], (3 * k + 1) & 3), K.inv[1], K.ninv[1]);
+    const float m2 = fmaf(bytef(pw[(3 * k + 2) >> 2], (3 * k + 2) & 3), K.inv[2], K.ninv[2]);
+    return fmaxf(fmaf(-kp.omega, fminf(fminf(m0, m1), m2), 1.f), kp.t0);
+  } else if (tsrc == TS_FAST) {
+    const float i0 = bytef(iw[(3 * k) >> 2], (3 * k) & 3);
+    const float i1 = bytef(iw[(3 * k + 1) >> 2], (3 * k + 1) & 3);
+    const float i2 = bytef(iw[(3 * k + 2) >> 2], (3 * k + 2) & 3);
+    const float mu = fmaf(fminf(fminf(i0, i1), i2), K.inv_fast, K.ninv_fast);
+    return fmaxf(fmaf(-kp.omega, mu, 1.f), kp.t0);
+  } else if (tsrc == TS_PLANE32) {
+    return static_cast<const float*>(tp)[k];
+  } else {
+    return __half2float(static_cast<const __half*>(tp)[k]);
+  }
+}
+
+// gamma-corrected (and, for M_BAL_APPLY, balanced) value of one channel
+template <int MODE>
+__device__ __forceinline__ float jg_of(float vbits, int c, float rt, const P3Const& K, const HzKParams& kp) {
+  const float In = fmaf(vbits, INV255, -TWO23 * INV255);
+  const float J = __saturatef(fmaf(In - K.A[c], rt, K.A[c]));
+  float Jg = kp.gamma_is_one ? J : ex2a(kp.gamma_inv * lg2a(J));
+  if constexpr (MODE == M_BAL_APPLY) Jg = fminf(Jg * K.gains[c], 1.f);
+  return Jg;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   const HzJob& jb = jobs.j[blockIdx.y];
+  const int W = jb.W, H = jb.H;
+  const int gpr = (W + P3_GPX - 1) / P3_GPX;  // pixel groups per row
+  const long long ngroups = (long long)gpr * H;
+  const int nunits = int((ngroups + P3_THREADS - 1) / P3_THREADS);
   const int unit = blockIdx.x;
-  const int nunits = jb.H * jb.segs;
   if (unit >= nunits) return;
-  const int y = unit / jb.segs, s = unit - y * jb.segs;
   const int tid = threadIdx.x;
-  const int x = s * P3_SEG + P3_PX * tid;
-  const int W = jb.W;
-  HzFrameRec* rec = jb.rec;
-  const float A0 = rec->A[0], A1 = rec->A[1], A2 = rec->A[2];
-  float jsum0 = 0.f, jsum1 = 0.f, jsum2 = 0.f;
-  if (x < W) {
-    const int nv = min(P3_PX, W - x);
+  const long long g = (long long)unit * P3_THREADS + tid;
+  const HzFrameRec* rec = jb.rec;
+  P3Const K;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    K.A[c] = rec->A[c];
+    K.inv[c] = rec->inv[c];
+    K.ninv[c] = -TWO23 * K.inv[c];
+    K.gains[c] = (MODE == M_BAL_APPLY) ? rec->gains[c] : 1.f;
+  }
+  K.inv_fast = rec->inv_fast;
+  K.ninv_fast = -TWO23 * K.inv_fast;
+  float js0 = 0.f, js1 = 0.f, js2 = 0.f;
+  if (g < ngroups) {
+    const int y = int(g / gpr);
+    const int x = int(g - (long long)y * gpr) * P3_GPX;
+    const int nv = min(P3_GPX, W - x);
     const uint8_t* Ip = jb.in + (long long)y * jb.in_pitch + 3LL * x;
-    const bool ia = ((reinterpret_cast<uintptr_t>(Ip) & 3) == 0);
-    uint32_t iw[3];
-    load12(Ip, ia, nv, iw);
-    float t[4];
-    if (jb.tsrc == TS_P) {
-      const uint32_t* Pp = reinterpret_cast<const uint32_t*>(jb.P + (long long)y * jb.P_pitch + 3LL * x);
-      uint32_t pw[3] = {__ldcs(Pp), __ldcs(Pp + 1), __ldcs(Pp + 2)};
-      const float i0 = rec->inv[0], i1 = rec->inv[1], i2 = rec->inv[2];
+    const uint8_t* Pp = jb.P + (long long)y * jb.P_pitch + 3LL * x;
+    const void* tp = nullptr;
+    if (jb.tsrc == TS_PLANE32)
+      tp = reinterpret_cast<const float*>(static_cast<const uint8_t*>(jb.tplane) + (long long)y * jb.t_pitch) + x;
+    else if (jb.tsrc == TS_PLANE16)
+      tp = reinterpret_cast<const __half*>(static_cast<const uint8_t*>(jb.tplane) + (long long)y * jb.t_pitch) + x;
+    uint32_t iw[12], pw[12];
+    const bool vec = (nv == P3_GPX) && ((reinterpret_cast<uintptr_t>(Ip) & 15) == 0);
+    if (vec) {
+      const uint4* q = reinterpret_cast<const uint4*>(Ip);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float mu = fminf(fminf(float(byte_of(pw, 3 * k)) * i0, float(byte_of(pw, 3 * k + 1)) * i1),
-                               float(byte_of(pw, 3 * k + 2)) * i2);
-        t[k] = fmaxf(1.f - kp.omega * mu, kp.t0);
+      for (int k = 0; k < 3; ++k) {
+        const uint4 v = __ldcs(q + k);
+        iw[4 * k] = v.x; iw[4 * k + 1] = v.y; iw[4 * k + 2] = v.z; iw[4 * k + 3] = v.w;
       }
-    } else if (jb.tsrc == TS_FAST) {
-      const float iv = rec->inv_fast;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const unsigned mn = min(min(byte_of(iw, 3 * k), byte_of(iw, 3 * k + 1)), byte_of(iw, 3 * k + 2));
-        t[k] = fmaxf(1.f - kp.omega * (float(mn) * iv), kp.t0);
-      }
-    } else if (jb.tsrc == TS_PLANE32) {
-      const float* tp = reinterpret_cast<const float*>(static_cast<const uint8_t*>(jb.tplane) +
-                                                       (long long)y * jb.t_pitch) + x;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) t[k] = (k < nv) ? tp[k] : 1.f;
     } else {
-      const __half* tp = reinterpret_cast<const __half*>(static_cast<const uint8_t*>(jb.tplane) +
-                                                         (long long)y * jb.t_pitch) + x;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) t[k] = (k < nv) ? __half2float(tp[k]) : 1.f;
+      for (int k = 0; k < 12; ++k) iw[k] = 0u;
+#pragma unroll
+      for (int i = 0; i < 3 * P3_GPX; ++i)
+        if (i < 3 * nv) iw[i >> 2] |= uint32_t(Ip[i]) << (8 * (i & 3));
+    }
+    if (jb.tsrc == TS_P) {
+      const uint4* q = reinterpret_cast<const uint4*>(Pp);  // P rows: 128-byte pitch, padded
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint4 v = __ldcs(q + k);
+        pw[4 * k] = v.x; pw[4 * k + 1] = v.y; pw[4 * k + 2] = v.z; pw[4 * k + 3] = v.w;
+      }
     }
     if constexpr (MODE == M_T_ONLY) {
       uint8_t* trow = static_cast<uint8_t*>(jb.tplane) + (long long)y * jb.t_pitch;
-      if (jb.t_half_out) {
-        __half* tp = reinterpret_cast<__half*>(trow) + x;
-        for (int k = 0; k < nv; ++k) tp[k] = __float2half_rn(t[k]);
-      } else {
-        float* tp = reinterpret_cast<float*>(trow) + x;
-        for (int k = 0; k < nv; ++k) tp[k] = t[k];
+#pragma unroll
+      for (int k = 0; k < P3_GPX; ++k) {
+        if (k < nv) {
+          const float t = t_of(jb.tsrc, iw, pw, tp, k, K, kp);
+          if (jb.t_half_out) reinterpret_cast<__half*>(trow)[x + k] = __float2half_rn(t);
+          else reinterpret_cast<float*>(trow)[x + k] = t;
+        }
       }
     } else {
-      const float Af[3] = {A0, A1, A2};
-      const float gs[3] = {rec->gains[0], rec->gains[1], rec->gains[2]};
-      uint32_t ow[3] = {0u, 0u, 0u};
+      float q[4];
+      uint32_t ow[12];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float rt = __fdividef(1.f, t[k]);
+      for (int k = 0; k < P3_GPX; ++k) {
+        const float t = (k < nv) ? t_of(jb.tsrc, iw, pw, tp, k, K, kp) : 1.f;
+        const float rt = rcpa(t);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int bi = 3 * k + c;
-          const float In = float(byte_of(iw, bi)) * (1.f / 255.f);
-          float J = __saturatef(fmaf(In - Af[c], rt, Af[c]));
-          float Jg = kp.gamma_is_one ? J : __powf(J, kp.gamma_inv);
+          const int b = 3 * k + c;
+          const float Jg = jg_of<MODE>(bytef(iw[b >> 2], b & 3), c, rt, K, kp);
           if constexpr (MODE == M_BAL_SUMS) {
             if (k < nv) {
-              if (c == 0) jsum0 += Jg;
-              else if (c == 1) jsum1 += Jg;
-              else jsum2 += Jg;
+              if (c == 0) js0 += Jg;
+              else if (c == 1) js1 += Jg;
+              else js2 += Jg;
             }
           } else {
-            if constexpr (MODE == M_BAL_APPLY) Jg = fminf(Jg * gs[c], 1.f);
-            const unsigned o = __float2uint_rn(255.f * Jg);
-            ow[bi >> 2] |= (o & 0xffu) << (8 * (bi & 3));
+            q[b & 3] = fmaf(Jg, 255.f, MAGIC_RINT);
+            if ((b & 3) == 3) ow[b >> 2] = pack4(q[0], q[1], q[2], q[3]);
           }
         }
       }
       if constexpr (MODE == M_OUT || MODE == M_BAL_APPLY) {
         uint8_t* Op = jb.out + (long long)y * jb.out_pitch + 3LL * x;
-        const bool oa = ((reinterpret_cast<uintptr_t>(Op) & 3) == 0);
-        store12(Op, oa, nv, ow);
+        if (nv == P3_GPX && ((reinterpret_cast<uintptr_t>(Op) & 15) == 0)) {
+          uint4* o = reinterpret_cast<uint4*>(Op);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) __stcs(o + k, make_uint4(ow[4 * k], ow[4 * k + 1], ow[4 * k + 2], ow[4 * k + 3]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 3 * P3_GPX; ++i)
+            if (i < 3 * nv) Op[i] = uint8_t(byte_of(ow, i));
+        }
       }
     }
   }
   if constexpr (MODE == M_BAL_SUMS) {
     __shared__ double shd[8];
     __shared__ int s_last;
-    const double d0 = block_sum256((double)jsum0, shd);
-    const double d1 = block_sum256((double)jsum1, shd);
-    const double d2 = block_sum256((double)jsum2, shd);
+    HzFrameRec* wrec = jb.rec;
+    const double d0 = block_sum256((double)js0, shd);
+    const double d1 = block_sum256((double)js1, shd);
+    const double d2 = block_sum256((double)js2, shd);
     if (tid == 0) {
       jb.bal_part[3 * unit + 0] = d0;
       jb.bal_part[3 * unit + 1] = d1;
@@ -668,7 +768,7 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&rec->done_p3, 1u) == unsigned(nunits) - 1u);
+    if (tid == 0) s_last = (atomicAdd(&wrec->done_p3, 1u) == unsigned(nunits) - 1u);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -687,8 +787,8 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
       const double mu[3] = {t0 / N, t1 / N, t2 / N};
       const double mm = (mu[0] + mu[1] + mu[2]) / 3.0;
       for (int c = 0; c < 3; ++c) {
-        rec->mean_jg[c] = float(mu[c]);
-        rec->gains[c] = (mu[c] > 0.0) ? float(mm / mu[c]) : 1.f;
+        wrec->mean_jg[c] = float(mu[c]);
+        wrec->gains[c] = (mu[c] > 0.0) ? float(mm / mu[c]) : 1.f;
       }
     }
   }

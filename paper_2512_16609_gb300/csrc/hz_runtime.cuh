@@ -124,7 +124,7 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     f.H = Hs[i];
     f.tiles_x = (f.W + P1_TW - 1) / P1_TW;
     f.tiles_y = (f.H + P1_TH - 1) / P1_TH;
-    f.segs = (f.W + P3_SEG - 1) / P3_SEG;
+    f.segs = p3_units(f.W, f.H);
     f.K = num_top((long long)f.W * f.H, prm.top_fraction);
     f.P_pitch = (long long)align_up(size_t(3) * P1_TW * f.tiles_x, 128);
     f.off_rec = z;
@@ -145,7 +145,7 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     f.off_bal = 0;
     if (balance) {
       f.off_bal = o;
-      o = align_up(o + sizeof(double) * 3 * size_t(f.H) * f.segs, 256);
+      o = align_up(o + sizeof(double) * 3 * size_t(f.segs), 256);
     }
     f.off_t = f.off_vs = f.off_a = f.off_b = f.off_q = 0;
     f.plane_pitch32 = (long long)align_up(size_t(4) * f.W, 128);
