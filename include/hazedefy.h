@@ -254,6 +254,8 @@ typedef struct hz_server_stats {
   double busy_s;       /* wall time from the first submit to the last completion */
 } hz_server_stats;
 hz_status hz_get_server_stats(hz_ctx* ctx, hz_server_stats* out);
+/* Clear the latency samples and counters (streams and queues are kept). */
+hz_status hz_reset_server_stats(hz_ctx* ctx);
 
 /* ---------------------------------------------------------- profiling -- */
 /* Kernel classes of the path, for launch counts and timing. */

@@ -140,6 +140,7 @@ _SIGS = {
     "hz_stream_set_state": (C.c_int, [_P, _I, _P, _SZ]),
     "hz_get_server_stats": (C.c_int, [_P, C.POINTER(hz_server_stats)]),
     "hz_dehaze_frame_noalloc": (C.c_int, [C.POINTER(hz_params), _P, _I, _I, _SZ, _P, _SZ, _P, C.c_char_p, _SZ]),
+    "hz_reset_server_stats": (C.c_int, [_P]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
     "hz_get_profile": (C.c_int, [_P, C.POINTER(hz_profile), C.c_int]),
 }
@@ -432,3 +433,7 @@ def hz_dehaze_frame_noalloc(p: hz_params, inp, out, stream=None):
     if st != HZ_OK:
         raise HzError(st, f"hz_dehaze_frame_noalloc: {hz_status_str(st)}: {err.value.decode()}")
     return st
+
+
+def hz_reset_server_stats(ctx):
+    return _check(lib().hz_reset_server_stats(ctx), ctx, "hz_reset_server_stats")

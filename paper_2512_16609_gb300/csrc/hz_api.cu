@@ -49,7 +49,7 @@ hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s) {
 
 template <int R>
 static cudaError_t set_attr_one() {
-  return cudaFuncSetAttribute(k_p1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, P1G<R>::SMEM);
+  return cudaFuncSetAttribute(k_p1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, P1S<R>::SMEM);
 }
 
 hz_status set_p1_attributes(hz_ctx* c) {
@@ -66,7 +66,7 @@ hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& j
   LaunchScope ls(c, HZ_K_DARK, s);
   switch (R) {
 #define HZ_P1_CASE(r) \
-  case r: k_p1<r><<<grid, P1_THREADS, P1G<r>::SMEM, s>>>(jobs); break;
+  case r: k_p1<r><<<grid, P1S<r>::NT, P1S<r>::SMEM, s>>>(jobs); break;
     HZ_P1_CASE(0) HZ_P1_CASE(1) HZ_P1_CASE(2) HZ_P1_CASE(3) HZ_P1_CASE(4) HZ_P1_CASE(5)
     HZ_P1_CASE(6) HZ_P1_CASE(7) HZ_P1_CASE(8) HZ_P1_CASE(9) HZ_P1_CASE(10) HZ_P1_CASE(11)
     HZ_P1_CASE(12) HZ_P1_CASE(13) HZ_P1_CASE(14) HZ_P1_CASE(15)
@@ -96,14 +96,15 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     const FramePlan& f = lp.fp[i];
     HzJob& j = jobs.j[i];
     j = HzJob{};
-    j.in = fr[i].in;
+    j.in = f.off_copy ? A + f.off_copy : fr[i].in;
     j.out = fr[i].out;
-    j.in_pitch = (long long)fr[i].in_pitch;
+    j.in_pitch = f.off_copy ? f.copy_pitch : (long long)fr[i].in_pitch;
     j.out_pitch = (long long)fr[i].out_pitch;
     j.W = f.W;
     j.H = f.H;
     j.tiles_x = f.tiles_x;
     j.tiles_y = f.tiles_y;
+    j.band_h = f.band_h;
     j.segs = f.segs;
     j.tsrc = tsrc_video;
     j.K = f.K;
@@ -123,6 +124,17 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.use_override = c->prm.use_airlight_override;
     j.t_half_out = 0;
   }
+}
+
+cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base, cudaStream_t s) {
+  for (int i = 0; i < n; ++i) {
+    const FramePlan& f = lp.fp[i];
+    if (!f.off_copy) continue;
+    cudaError_t e = cudaMemcpy2DAsync(base + f.off_copy, size_t(f.copy_pitch), fr[i].in, fr[i].in_pitch,
+                                      size_t(3) * f.W, size_t(f.H), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static int max_tiles(const HzJobs& jobs) {
@@ -263,12 +275,15 @@ hz_status run_image_job(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool bala
 
 hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_frame_info* infos, bool balance) {
   if (!infos) return HZ_OK;
-  for (int i = 0; i < n; ++i)
-    HZ_CK(c, cudaMemcpyAsync(c->rec_host + i, c->arena.base + lp.fp[i].off_rec, sizeof(HzFrameRec),
-                             cudaMemcpyDeviceToHost, s));
+  HZ_CK(c, cudaMemcpyAsync(c->rec_host, c->arena.base, sizeof(HzFrameRec) * size_t(n), cudaMemcpyDeviceToHost, s));
   HZ_CK(c, cudaStreamSynchronize(s));
+  recs_to_infos(c->rec_host, lp, n, infos, balance);
+  return HZ_OK;
+}
+
+void recs_to_infos(const HzFrameRec* recs, const LaunchPlan& lp, int n, hz_frame_info* infos, bool balance) {
   for (int i = 0; i < n; ++i) {
-    const HzFrameRec& r = c->rec_host[i];
+    const HzFrameRec& r = recs[i];
     hz_frame_info& o = infos[i];
     std::memset(&o, 0, sizeof o);
     for (int k = 0; k < 3; ++k) {
@@ -284,7 +299,6 @@ hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_
     o.T = r.T;
     o.status = r.status;
   }
-  return HZ_OK;
 }
 
 }  // namespace hz
@@ -457,11 +471,6 @@ static hz_status check_frame(hz_ctx* c, const void* in, int W, int H, size_t pit
   return HZ_OK;
 }
 
-#define HZ_TRY(expr)                  \
-  do {                                \
-    hz_status st_ = (expr);           \
-    if (st_ != HZ_OK) return st_;     \
-  } while (0)
 
 static hz_status check_stream_id(hz_ctx* c, int32_t sid) {
   if (sid == -1) return HZ_OK;
@@ -473,7 +482,7 @@ static hz_status check_stream_id(hz_ctx* c, int32_t sid) {
 
 // Video frames on device memory, chunked by MAXJ and an L2-sized wave.
 static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
-                              HzStreamState* chain) {
+                              HzStreamState* chain, HzFrameRec* rec_sink = nullptr) {
   const bool bal = c->prm.color_balance != 0;
   const int tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
   int i = 0;
@@ -494,13 +503,16 @@ static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStr
       Hs[k] = fr[i + k].H;
     }
     LaunchPlan lp;
-    plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp);
+    plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp, fr + i);
     HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+    HZ_CK(c, copy_unaligned(lp, fr + i, m, c->arena.base, s));
     HzJobs jobs;
     fill_jobs(c, lp, fr + i, m, jobs, tsrc);
     if (chain)
       for (int k = 0; k < m; ++k) jobs.j[k].state = chain;
     HZ_TRY(run_video_jobs(c, lp, jobs, bal, s));
+    if (rec_sink)
+      HZ_CK(c, cudaMemcpyAsync(rec_sink + i, c->arena.base, sizeof(HzFrameRec) * size_t(m), cudaMemcpyDeviceToHost, s));
     HZ_TRY(read_infos(c, lp, m, s, infos ? infos + i : nullptr, bal));
     i += m;
   }
@@ -522,6 +534,47 @@ extern "C" hz_status hz_dehaze_frame(hz_ctx* c, int32_t stream_id, const uint8_t
   return mark_done(c, s);
 }
 
+// Frames of a mixed batch: plain frames batched per launch, guided frames
+// through the image path one by one. order[k] = index in `frames` of the
+// k-th frame processed; rec_sink (pinned host, n records, optional) receives
+// the k-th frame's record in that order, copied on stream s.
+hz_status hz::run_batch(hz_ctx* c, const hz_frame_desc* frames, int n, cudaStream_t s, hz_frame_info* infos,
+                    HzFrameRec* rec_sink, int* order) {
+  std::vector<hz_frame_desc> plain;
+  std::vector<int> plain_idx;
+  for (int i = 0; i < n; ++i) {
+    if (frames[i].flags & HZ_GUIDED) continue;
+    plain.push_back(frames[i]);
+    plain_idx.push_back(i);
+  }
+  std::vector<hz_frame_info> pinfo(plain.size());
+  if (!plain.empty())
+    HZ_TRY(video_device(c, plain.data(), (int)plain.size(), s, infos ? pinfo.data() : nullptr, nullptr, rec_sink));
+  int k = 0;
+  for (size_t q = 0; q < plain.size(); ++q) {
+    if (infos) infos[plain_idx[q]] = pinfo[q];
+    if (order) order[k] = plain_idx[q];
+    ++k;
+  }
+  const bool bal = c->prm.color_balance != 0;
+  for (int i = 0; i < n; ++i) {
+    if (!(frames[i].flags & HZ_GUIDED)) continue;
+    LaunchPlan lp;
+    plan_frames(c->prm, &frames[i].W, &frames[i].H, 1, true, bal, lp, frames + i);
+    HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+    HZ_CK(c, copy_unaligned(lp, frames + i, 1, c->arena.base, s));
+    HzJobs jobs;
+    fill_jobs(c, lp, frames + i, 1, jobs, TS_P);
+    HZ_TRY(run_image_job(c, lp, jobs, bal, s));
+    if (rec_sink)
+      HZ_CK(c, cudaMemcpyAsync(rec_sink + k, c->arena.base, sizeof(HzFrameRec), cudaMemcpyDeviceToHost, s));
+    HZ_TRY(read_infos(c, lp, 1, s, infos ? infos + i : nullptr, bal));
+    if (order) order[k] = i;
+    ++k;
+  }
+  return HZ_OK;
+}
+
 extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
                                      hz_frame_info* infos) {
   if (!c) return HZ_EINVAL;
@@ -536,30 +589,7 @@ extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
-  // guided frames go one by one through the image path; the rest batched
-  std::vector<hz_frame_desc> plain;
-  std::vector<int> plain_idx;
-  for (int i = 0; i < n; ++i) {
-    if (frames[i].flags & HZ_GUIDED) continue;
-    plain.push_back(frames[i]);
-    plain_idx.push_back(i);
-  }
-  std::vector<hz_frame_info> pinfo(plain.size());
-  if (!plain.empty())
-    HZ_TRY(video_device(c, plain.data(), (int)plain.size(), s, infos ? pinfo.data() : nullptr, nullptr));
-  if (infos)
-    for (size_t k = 0; k < plain.size(); ++k) infos[plain_idx[k]] = pinfo[k];
-  const bool bal = c->prm.color_balance != 0;
-  for (int i = 0; i < n; ++i) {
-    if (!(frames[i].flags & HZ_GUIDED)) continue;
-    LaunchPlan lp;
-    plan_frames(c->prm, &frames[i].W, &frames[i].H, 1, true, bal, lp);
-    HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
-    HzJobs jobs;
-    fill_jobs(c, lp, frames + i, 1, jobs, TS_P);
-    HZ_TRY(run_image_job(c, lp, jobs, bal, s));
-    HZ_TRY(read_infos(c, lp, 1, s, infos ? infos + i : nullptr, bal));
-  }
+  HZ_TRY(run_batch(c, frames, n, s, infos, nullptr, nullptr));
   return mark_done(c, s);
 }
 
@@ -649,9 +679,10 @@ extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, in
   HZ_TRY(order_after_previous(c, s));
   const bool bal = c->prm.color_balance != 0;
   LaunchPlan lp;
-  plan_frames(c->prm, &W, &H, 1, true, bal, lp);
-  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
   hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, -1, HZ_GUIDED};
+  plan_frames(c->prm, &W, &H, 1, true, bal, lp, &d);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  HZ_CK(c, copy_unaligned(lp, &d, 1, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   HZ_TRY(run_image_job(c, lp, jobs, bal, s));
@@ -671,9 +702,10 @@ extern "C" hz_status hz_dark_channel(hz_ctx* c, const uint8_t* in, int32_t W, in
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
   LaunchPlan lp;
-  plan_frames(c->prm, &W, &H, 1, false, false, lp);
-  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
   hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  plan_frames(c->prm, &W, &H, 1, false, false, lp, &d);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  HZ_CK(c, copy_unaligned(lp, &d, 1, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   jobs.j[0].Dout = D;
@@ -693,9 +725,10 @@ extern "C" hz_status hz_estimate_airlight(hz_ctx* c, const uint8_t* in, int32_t 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
   LaunchPlan lp;
-  plan_frames(c->prm, &W, &H, 1, false, false, lp);
-  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
   hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  plan_frames(c->prm, &W, &H, 1, false, false, lp, &d);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  HZ_CK(c, copy_unaligned(lp, &d, 1, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   jobs.j[0].use_override = 0;
@@ -710,9 +743,10 @@ static hz_status stage_with_A(hz_ctx* c, const uint8_t* in, int W, int H, size_t
   if (!A) return fail(c, HZ_EINVAL, "A is NULL");
   for (int k = 0; k < 3; ++k)
     if (!(A[k] > 0.f) || !(A[k] <= 1.f)) return fail(c, HZ_EINVAL, "A must be in (0, 1]");
-  plan_frames(c->prm, &W, &H, 1, false, c->prm.color_balance != 0, lp);
-  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
   hz_frame_desc d{in, in_pitch, nullptr, 0, W, H, -1, 0u};
+  plan_frames(c->prm, &W, &H, 1, false, c->prm.color_balance != 0, lp, &d);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  HZ_CK(c, copy_unaligned(lp, &d, 1, c->arena.base, s));
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   jobs.j[0].use_override = 1;
   HzKParams kp = kparams_of(c->prm);
@@ -929,7 +963,8 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   }
   const bool bal = p->color_balance != 0;
   LaunchPlan lp;
-  plan_frames(*p, &W, &H, 1, false, bal, lp);
+  const hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, -1, 0u};
+  plan_frames(*p, &W, &H, 1, false, bal, lp, &d);
   if (lp.total > NOALLOC_SCRATCH_BYTES) {
     noalloc_msg(err, err_len, "a %dx%d frame needs %zu bytes of scratch; the static scratch holds %zu", W, H,
                 lp.total, NOALLOC_SCRATCH_BYTES);
@@ -952,14 +987,15 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   HzJob& j = jobs.j[0];
   const FramePlan& f = lp.fp[0];
   j = HzJob{};
-  j.in = in;
+  j.in = f.off_copy ? base + f.off_copy : in;
   j.out = out;
-  j.in_pitch = (long long)in_pitch;
+  j.in_pitch = f.off_copy ? f.copy_pitch : (long long)in_pitch;
   j.out_pitch = (long long)out_pitch;
   j.W = W;
   j.H = H;
   j.tiles_x = f.tiles_x;
   j.tiles_y = f.tiles_y;
+  j.band_h = f.band_h;
   j.segs = f.segs;
   j.tsrc = (p->t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
   j.K = f.K;
@@ -977,12 +1013,13 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   // the counters, histogram and per-row sums of the previous call must not
   // leak into this one
   cudaError_t e = cudaMemsetAsync(base, 0, lp.zero_bytes, s);
+  if (e == cudaSuccess) e = copy_unaligned(lp, &d, 1, base, s);
   const dim3 g1(f.tiles_x * f.tiles_y, 1);
   const dim3 g3(f.segs, 1);
   if (e == cudaSuccess) {
     switch (p->patch / 2) {
 #define HZ_NA_P1(r) \
-  case r: k_p1<r><<<g1, P1_THREADS, P1G<r>::SMEM, s>>>(jobs); break;
+  case r: k_p1<r><<<g1, P1S<r>::NT, P1S<r>::SMEM, s>>>(jobs); break;
       HZ_NA_P1(0) HZ_NA_P1(1) HZ_NA_P1(2) HZ_NA_P1(3) HZ_NA_P1(4) HZ_NA_P1(5) HZ_NA_P1(6) HZ_NA_P1(7)
       HZ_NA_P1(8) HZ_NA_P1(9) HZ_NA_P1(10) HZ_NA_P1(11) HZ_NA_P1(12) HZ_NA_P1(13) HZ_NA_P1(14) HZ_NA_P1(15)
 #undef HZ_NA_P1

@@ -18,10 +18,14 @@
 
 namespace hz {
 
-// ---- tiling of the dark-channel / selection kernels --------------------
-constexpr int P1_TW = 128;      // tile width in pixels (multiple of 32)
-constexpr int P1_TH = 32;       // tile height in rows
-constexpr int P1_THREADS = 256;
+// ---- dark-channel regions ------------------------------------------------
+constexpr int P1_SW = 320;     // output pixels per strip (multiple of 64)
+// Output blocks of 2R+1 rows per dark-channel band: the staged band
+// ((blocks + 1) (2R+1) rows) stays near 64 rows.
+__host__ __device__ constexpr int p1_band_blocks(int R) {
+  return (64 / (2 * R + 1) - 1) < 1 ? 1 : (64 / (2 * R + 1) - 1);
+}
+__host__ __device__ constexpr int p1_band_rows(int R) { return p1_band_blocks(R) * (2 * R + 1); }
 // ---- pointwise reconstruction kernels ----------------------------------
 constexpr int P3_THREADS = 256;
 constexpr int P3_GPX = 16;                      // pixels per thread (48 bytes of I)
@@ -38,9 +42,10 @@ constexpr int GF_HRUN = 8;      // consecutive outputs per thread
 
 constexpr float A_FLOOR = 1e-6f;  // airlight floor used in ratios I/A
 constexpr int HZ_STATUS_SELECT_FAILED = -100;  // per-frame status: selection inconsistent
+constexpr int HZ_STATUS_DEVICE_TIMEOUT = -6;   // per-frame status: a bounded device wait gave up
 
 // Per-frame record, zeroed before each launch that uses it.
-struct HzFrameRec {
+struct __align__(16) HzFrameRec {
   unsigned hist[256];           // histogram of D
   unsigned done_p1, done_p2, done_p3, done_pad;
   int T;                        // threshold level
@@ -59,6 +64,7 @@ struct HzFrameRec {
   float mean_jg[3];
   float pad2;
 };
+static_assert(sizeof(HzFrameRec) % 16 == 0, "records are packed in arrays");
 
 // Airlight smoothing state of one stream (48 bytes; matches the size the
 // C interface exports for checkpointing).
@@ -80,7 +86,8 @@ struct HzJob {
   uint8_t* out;
   long long in_pitch, out_pitch;
   int W, H;
-  int tiles_x, tiles_y;         // dark-channel tiling
+  int tiles_x, tiles_y;         // dark-channel regions: strips x bands
+  int band_h;                   // output rows per band
   int segs;                     // reconstruction blocks of the frame (p3_units)
   int tsrc;                     // TSource for the reconstruction pass
   long long K;

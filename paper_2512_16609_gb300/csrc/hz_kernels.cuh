@@ -32,27 +32,6 @@ __device__ __forceinline__ void slide_min(uint32_t (&v)[L]) {
   }
 }
 
-template <int R>
-struct P1G {
-  static constexpr int P = 2 * R + 1;
-  static constexpr int RA = (R + 3) & ~3;       // horizontal halo, multiple of 4
-  static constexpr int EW = P1_TW + 2 * RA;     // staged width (px)
-  static constexpr int EH = P1_TH + 2 * R;      // staged height (rows)
-  static constexpr int EWW = EW / 2;            // u16x2 words per planar row
-  static constexpr int PLW = EWW | 1;           // odd word pitch
-  static constexpr int RAWP = ((3 * EW + 48 + 15) / 16) * 16;
-  static constexpr int RAW_BYTES = EH * RAWP;
-  static constexpr int POUT_W = P1_TW / 2;
-  static constexpr int POUT_BYTES = 3 * P1_TH * POUT_W * 4;
-  static constexpr int U_BYTES = RAW_BYTES > POUT_BYTES ? RAW_BYTES : POUT_BYTES;
-  static constexpr int PL_BYTES = 3 * EH * PLW * 4;
-  static constexpr int HIST_BYTES = (P1_THREADS / 32) * 256 * 4;
-  static constexpr int SEG = (R <= 7) ? 16 : 8;  // output words per horizontal item
-  static constexpr int E0 = RA - R;              // first staged px a window needs
-  static constexpr int CHMAX = (3 * EW + 30) / 16 + 2;
-  static constexpr int SMEM = U_BYTES + PL_BYTES + HIST_BYTES + EH * 4 + 32;
-};
-
 // Block-wide inclusive scan of one unsigned per thread (blockDim 256).
 __device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* sh /*>= 8*/, unsigned* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -91,245 +70,395 @@ __device__ __forceinline__ T block_sum256(T v, T* sh /*>= 8*/) {
 }
 
 // ------------------------------------------------------------------------
-// p1: one TW x TH tile of one frame.
+// p1: one strip x band region of one frame (SW output pixels wide, band_h
+// output rows tall), streamed row by row.
+//
+//  * Rows of the staged strip (SW + 2 RA pixels, RA = R rounded up to 4)
+//    arrive in shared memory by TMA bulk copies (cp.async.bulk, one per row,
+//    16-byte aligned source span), completed on an mbarrier per buffer.
+//  * Vertical minimum: each thread owns one 4-byte column of the staged rows
+//    and runs van Herk / Gil-Werman over blocks of p = 2R + 1 rows in
+//    registers (prefix running minimum, suffix minima of the previous block:
+//    three u16x2 minima per value). The 4 interleaved bytes of a column are
+//    two u16x2 views, w (bytes 1 and 3 in the lanes' high bytes) and w << 8
+//    (bytes 0 and 2); the low bytes are don't-care and never change the high
+//    byte of a lane minimum.
+//  * Horizontal minimum: per run of 20 output pixels, each pixel becomes an
+//    RGBX word (one PRMT) split into the same two views, and the window
+//    minimum along pixels is taken by doubling windows on those arrays.
+//  * Epilogue: P bytes (RGB) straight to global memory, D = min_c P^c,
+//    warp-private histogram (run-length merged), region maximum; the last
+//    region of a frame derives T, n_above and m_ties (Eq. 3 set).
+
+constexpr int P1_HSEG = 64;              // output pixels per horizontal item
+constexpr int P1_NSEG = P1_SW / P1_HSEG;  // horizontal items per row
+
 template <int R>
-__device__ __forceinline__ void p1_tile(const HzJob& jb, int tile, unsigned char* smem) {
-  using G = P1G<R>;
+struct P1S {
+  static constexpr int P = 2 * R + 1;
+  static constexpr int M = p1_band_blocks(R);                   // output blocks per band
+  static constexpr int BH = M * P;                              // output rows per band
+  static constexpr int NROWS = (M + 1) * P;                     // staged rows
+  static constexpr int NBLK = (P >= 8) ? 1 : (8 + P - 1) / P;   // vHGW blocks per barrier
+  static constexpr int CH = NBLK * P;                           // staged rows per barrier
+  static constexpr int NCH = (M + 1 + NBLK - 1) / NBLK;         // barriers
+  static constexpr int RA = (R + 3) & ~3;
+  static constexpr int EW = P1_SW + 2 * RA;                     // staged pixels
+  static constexpr int NWC = 3 * EW / 4;                        // staged 4-byte columns
+  static constexpr int NT = ((NWC + 31) / 32) * 32;             // threads
+  static constexpr int SLOT = 16 * (((3 * EW + 48 + 15) / 16) | 1);  // bytes per staged row (16 x odd)
+  static constexpr int S0 = 16 + ((-3 * RA) & 15);              // slot byte of staged byte 0
+  static constexpr int IB0 = (S0 + 3 * (RA - R)) & ~15;         // item chunk base (+192 per segment)
+  static constexpr int E0B = (S0 + 3 * (RA - R)) & 15;          // byte of element 0 in that chunk
+  static constexpr int NCK = ((E0B + 3 * (P1_HSEG + 2 * R) + 3) >> 4) + 1;  // 16-byte chunks per item
+  static constexpr int NIN = P1_HSEG + 2 * R;                   // staged pixels per horizontal item
+  static constexpr int OFF_HIST = ((NCH * CH * SLOT) + 15) / 16 * 16;
+  static constexpr int OFF_MBAR = OFF_HIST + (NT / 32) * 256 * 4;
+  static constexpr int SMEM = OFF_MBAR + NCH * 8 + 16;
+};
+
+// staged copies (S0 + 3 EW + 15) and item chunk reads stay inside a slot
+template <int R>
+constexpr bool p1_bounds_ok() {
+  using G = P1S<R>;
+  return G::S0 + 3 * G::EW + 16 <= G::SLOT && G::IB0 + 3 * P1_HSEG * (P1_NSEG - 1) + 16 * G::NCK <= G::SLOT &&
+         (G::SLOT / 16) % 2 == 1 && G::NT <= 1024 && G::SMEM <= 227 * 1024 && G::NCH * G::CH <= G::NT;
+}
+static_assert(p1_bounds_ok<0>() && p1_bounds_ok<1>() && p1_bounds_ok<2>() && p1_bounds_ok<3>(), "p1 bounds");
+static_assert(p1_bounds_ok<4>() && p1_bounds_ok<5>() && p1_bounds_ok<6>() && p1_bounds_ok<7>(), "p1 bounds");
+static_assert(p1_bounds_ok<8>() && p1_bounds_ok<9>() && p1_bounds_ok<10>() && p1_bounds_ok<11>(), "p1 bounds");
+static_assert(p1_bounds_ok<12>() && p1_bounds_ok<13>() && p1_bounds_ok<14>() && p1_bounds_ok<15>(), "p1 bounds");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx_arrive(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait on a chunk's barrier: false when it gave up (the caller
+// records HZ_STATUS_DEVICE_TIMEOUT and abandons the region).
+constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity) {
+  for (unsigned it = 0; it < MBAR_SPIN_LIMIT; ++it)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
+
+// Stage every row of the band. Rows outside the frame (or past the last
+// needed row) are filled with 0xFF (+inf for minima) by the whole block;
+// every other row is one bulk copy (16-byte aligned span) issued by its own
+// thread, which arrives on its chunk's barrier with the copy's byte count
+// (barrier count = rows per chunk). Staged byte 0 of every row sits at slot
+// byte S0: frames are 16-byte aligned with a pitch that is a multiple of 16,
+// so every row's copy lands at the same offset.
+template <int R>
+__device__ __forceinline__ void p1_stage_band(const HzJob& jb, int ya, int nrows_need, int xs, int xa, int xb,
+                                              unsigned char* smem, uint64_t* mbar) {
+  using G = P1S<R>;
+  constexpr int NR = G::NCH * G::CH;
+  const int tid = threadIdx.x;
+  // rows [0, k_lo) and [k_hi, NR) hold no frame data
+  const int k_lo = min(NR, max(0, -ya));
+  const int k_hi = max(k_lo, min(NR, min(jb.H - ya, nrows_need)));
+  const bool empty = xa >= xb;
+  for (int k = 0; k < NR; ++k) {
+    if (k == k_lo && !empty) k = k_hi;
+    if (k >= NR) break;
+    uint32_t* row = reinterpret_cast<uint32_t*>(smem + k * G::SLOT);
+    for (int q = tid; q < G::SLOT / 4; q += G::NT) row[q] = 0xffffffffu;
+  }
+  if (tid < NR) {
+    const int k = tid, c = k / G::CH;
+    unsigned bytes = 0;
+    const void* src = nullptr;
+    unsigned char* dst = nullptr;
+    if (!empty && k >= k_lo && k < k_hi) {
+      const uintptr_t rowp = reinterpret_cast<uintptr_t>(jb.in) + uintptr_t(ya + k) * uintptr_t(jb.in_pitch);
+      const uintptr_t a0 = (rowp + uintptr_t(3 * xa)) & ~uintptr_t(15);
+      const uintptr_t a1 = (rowp + uintptr_t(3 * xb) + 15) & ~uintptr_t(15);
+      const uintptr_t base = rowp + uintptr_t(3 * (long long)xs);  // staged byte 0
+      bytes = unsigned(a1 - a0);
+      src = reinterpret_cast<const void*>(a0);
+      dst = smem + k * G::SLOT + G::S0 + (long long)(a0 - base);
+    }
+    mbar_expect_tx_arrive(mbar + c, bytes);
+    if (bytes) bulk_g2s(dst, src, bytes, mbar + c);
+  }
+}
+
+// Vertical minimum of one block of P staged rows for column j (two views),
+// streaming van Herk / Gil-Werman; the outputs of the previous block replace
+// the staged words of that block (this column's words are never read again).
+template <int R>
+__device__ __forceinline__ void p1_vblock(unsigned char* smem, int B, int j, uint32_t (&hE)[2 * R + 1],
+                                          uint32_t (&hO)[2 * R + 1]) {
+  using G = P1S<R>;
+  constexpr int P = G::P;
+  uint32_t cE[P], cO[P];
+  uint32_t gE = 0u, gO = 0u;
+  const int col = G::S0 + 4 * j;
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(smem + (B * P + a) * G::SLOT + col);
+    const uint32_t xE = w << 8, xO = w;
+    if (B >= 1) {
+      const uint32_t oE = (a == 0) ? hE[0] : vmin2(hE[a], gE);
+      const uint32_t oO = (a == 0) ? hO[0] : vmin2(hO[a], gO);
+      *reinterpret_cast<uint32_t*>(smem + ((B - 1) * P + a) * G::SLOT + col) = __byte_perm(oE, oO, 0x7351u);
+    }
+    gE = (a == 0) ? xE : vmin2(gE, xE);
+    gO = (a == 0) ? xO : vmin2(gO, xO);
+    cE[a] = xE;
+    cO[a] = xO;
+  }
+  hE[P - 1] = cE[P - 1];
+  hO[P - 1] = cO[P - 1];
+#pragma unroll
+  for (int a = P - 2; a >= 0; --a) {
+    hE[a] = vmin2(cE[a], hE[a + 1]);
+    hO[a] = vmin2(cO[a], hO[a + 1]);
+  }
+}
+
+// One horizontal item: streaming van Herk / Gil-Werman along the staged
+// pixels e: output u = e - 2R covers elements u..e; with e at position a of
+// block e / P it is min(suffix of the previous block from a + 1, prefix of
+// this block through e), or, when a = P - 1, the whole block. The V row is
+// read in 16-byte chunks (a 16 x odd byte row pitch keeps the lanes, one row
+// each, on distinct bank groups), each chunk loaded once, when first needed.
+// EDGE items mask pixels outside the frame, stop at the frame's right edge
+// and may write the dark channel D.
+template <int R, bool EDGE>
+__device__ __forceinline__ void p1_hitem(const uint4* vq, int sp0, int W, int nv, uint4* Pp, uint8_t* Dp,
+                                         unsigned* hw, unsigned& tmax) {
+  using G = P1S<R>;
+  constexpr int P = G::P;
+  unsigned cur = 0u, cnt = 0u;
+  uint32_t hE[P], hO[P], cE[P], cO[P];
+  uint32_t gE = 0u, gO = 0u;
+  uint32_t Cb[4];
+  uint32_t Wb[12];
+  uint32_t wv[4 * G::NCK];
+#pragma unroll
+  for (int e = 0; e < G::NIN; ++e) {
+    const int a = e % P;
+    const int b = G::E0B + 3 * e;
+    const int w0 = b >> 2;
+    // chunks needed through word w0 + 1, loaded the first time they are
+    const int need = (w0 + 1) >> 2;
+    const int have = (e == 0) ? -1 : ((((G::E0B + 3 * (e - 1)) >> 2) + 1) >> 2);
+#pragma unroll
+    for (int q = 0; q < G::NCK; ++q) {
+      if (q > have && q <= need) {
+        const uint4 v = vq[q];
+        wv[4 * q] = v.x; wv[4 * q + 1] = v.y; wv[4 * q + 2] = v.z; wv[4 * q + 3] = v.w;
+      }
+    }
+    uint32_t x = __byte_perm(wv[w0], wv[w0 + 1], 0x3210u + 0x1111u * uint32_t(b & 3));
+    if (EDGE && (sp0 + e < 0 || sp0 + e >= W)) x = 0xffffffffu;
+    const uint32_t xE = x << 8, xO = x;
+    gE = (a == 0) ? xE : vmin2(gE, xE);
+    gO = (a == 0) ? xO : vmin2(gO, xO);
+    cE[a] = xE;
+    cO[a] = xO;
+    if (a == P - 1) {
+      hE[P - 1] = cE[P - 1];
+      hO[P - 1] = cO[P - 1];
+#pragma unroll
+      for (int q = P - 2; q >= 0; --q) {
+        hE[q] = vmin2(cE[q], hE[q + 1]);
+        hO[q] = vmin2(cO[q], hO[q + 1]);
+      }
+    }
+    const int u = e - 2 * R;
+    if (u >= 0) {
+      uint32_t oE, oO;
+      if (a == P - 1) {
+        oE = hE[0];
+        oO = hO[0];
+      } else {
+        oE = vmin2(hE[a + 1], gE);
+        oO = vmin2(hO[a + 1], gO);
+      }
+      Cb[u & 3] = __byte_perm(oE, oO, 0x7351u);  // r g b x
+      const unsigned dv = (vmin2(vmin2(oE, oO), oE >> 16) >> 8) & 0xffu;
+      if (!EDGE || u < nv) {
+        if (EDGE && Dp) Dp[u] = uint8_t(dv);
+        tmax = max(tmax, dv);
+        if (dv == cur) {
+          ++cnt;
+        } else {
+          if (cnt) atomicAdd(&hw[cur], cnt);
+          cur = dv;
+          cnt = 1;
+        }
+      }
+      if ((u & 3) == 3) {
+        const int wq = 3 * ((u & 15) >> 2);
+        Wb[wq + 0] = __byte_perm(Cb[0], Cb[1], 0x4210u);
+        Wb[wq + 1] = __byte_perm(Cb[1], Cb[2], 0x5421u);
+        Wb[wq + 2] = __byte_perm(Cb[2], Cb[3], 0x6542u);
+      }
+      if ((u & 15) == 15) {
+        const int q16 = u >> 4;
+        Pp[3 * q16 + 0] = make_uint4(Wb[0], Wb[1], Wb[2], Wb[3]);
+        Pp[3 * q16 + 1] = make_uint4(Wb[4], Wb[5], Wb[6], Wb[7]);
+        Pp[3 * q16 + 2] = make_uint4(Wb[8], Wb[9], Wb[10], Wb[11]);
+      }
+    }
+  }
+  if (cnt) atomicAdd(&hw[cur], cnt);
+}
+
+template <int R>
+__device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned char* smem) {
+  using G = P1S<R>;
+  constexpr int P = G::P;
   const int tid = threadIdx.x;
   const int W = jb.W, H = jb.H;
-  const int tx = tile % jb.tiles_x, ty = tile / jb.tiles_x;
-  const int x0 = tx * P1_TW, y0 = ty * P1_TH;
-  const int xs = x0 - G::RA;
+  const int strip = item % jb.tiles_x, band = item / jb.tiles_x;
+  const int x0 = strip * P1_SW, y0 = band * G::BH;
+  const int bh = min(G::BH, H - y0);         // output rows of this region
+  const int xs = x0 - G::RA;                 // staged pixel 0
+  const int xa = max(xs, 0), xb = min(x0 + P1_SW + G::RA, W);
+  const int ya = y0 - R;                     // staged row 0
+  const int nblocks = (bh - 1) / P + 2;      // vHGW blocks (the first only primes)
+  const int nrows_need = bh + 2 * R;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MBAR);
+  unsigned* whist = reinterpret_cast<unsigned*>(smem + G::OFF_HIST);
+  __shared__ unsigned red[32];
+  __shared__ int s_last, s_fail;
 
-  uint8_t* raw = smem;                                              // staging / pout
-  uint32_t* pout = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* pl = reinterpret_cast<uint32_t*>(smem + G::U_BYTES);    // [3][EH][PLW]
-  unsigned* whist = reinterpret_cast<unsigned*>(smem + G::U_BYTES + G::PL_BYTES);
-  int* rowoff = reinterpret_cast<int*>(smem + G::U_BYTES + G::PL_BYTES + G::HIST_BYTES);
-  __shared__ unsigned red[8];
-  __shared__ int s_last;
-
-  for (int i = tid; i < (P1_THREADS / 32) * 256; i += P1_THREADS) whist[i] = 0u;
-
-  // ---- stage 1: aligned 16-byte copies of the staged rows -------------
-  const uintptr_t inb = reinterpret_cast<uintptr_t>(jb.in);
-  const int xa = max(xs, 0), xb = min(x0 + P1_TW + G::RA, W);
-  for (int e = tid; e < G::EH; e += P1_THREADS) {
-    const int y = y0 - R + e;
-    int off = -1;
-    if (y >= 0 && y < H) {
-      const uintptr_t rowp = inb + uintptr_t(y) * uintptr_t(jb.in_pitch);
-      off = 16 + int((rowp + uintptr_t(3 * (long long)xs)) & 15);
-    }
-    rowoff[e] = off;
-  }
-  for (int it = tid; it < G::EH * G::CHMAX; it += P1_THREADS) {
-    const int e = it / G::CHMAX, k = it - e * G::CHMAX;
-    const int y = y0 - R + e;
-    if (y < 0 || y >= H) continue;
-    const uintptr_t rowp = inb + uintptr_t(y) * uintptr_t(jb.in_pitch);
-    const uintptr_t g0 = rowp + uintptr_t(3 * xa), g1 = rowp + uintptr_t(3 * xb);
-    const uintptr_t a0 = g0 & ~uintptr_t(15), a1 = (g1 + 15) & ~uintptr_t(15);
-    const uintptr_t src = a0 + uintptr_t(16 * k);
-    if (src >= a1) continue;
-    const uintptr_t base = rowp + uintptr_t(3 * (long long)xs);
-    const int off = 16 + int(base & 15);
-    uint8_t* dst = raw + e * G::RAWP + off + (long long)(src - base);
-    const unsigned daddr = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(daddr), "l"(src));
-  }
-  asm volatile("cp.async.wait_all;\n" ::);
-  __syncthreads();
-
-  // ---- stage 2: deinterleave into u16x2 planes (value in the high byte) -
-  constexpr int GQ = G::EW / 4;
-  for (int it = tid; it < G::EH * GQ; it += P1_THREADS) {
-    const int e = it / GQ, q = it - e * GQ;
-    const int off = rowoff[e];
-    uint32_t w0 = 0xffffffffu, w1 = 0xffffffffu, w2 = 0xffffffffu, w3 = 0xffffffffu, w4 = 0xffffffffu,
-             w5 = 0xffffffffu;
-    if (off >= 0) {
-      const int b = off + 12 * q;
-      const uint32_t* r32 = reinterpret_cast<const uint32_t*>(raw + e * G::RAWP + (b & ~3));
-      const uint32_t sel = 0x3210u + 0x1111u * uint32_t(b & 3);
-      const uint32_t u0 = r32[0], u1 = r32[1], u2 = r32[2], u3 = r32[3];
-      const uint32_t v0 = prmt(u0, u1, sel), v1 = prmt(u1, u2, sel), v2 = prmt(u2, u3, sel);
-      // v0 = [r0 g0 b0 r1], v1 = [g1 b1 r2 g2], v2 = [b2 r3 g3 b3]
-      w0 = prmt(v0, v1, 0x3000u);  // r0 r1
-      w1 = prmt(v1, v2, 0x5020u);  // r2 r3
-      w2 = prmt(v0, v1, 0x4010u);  // g0 g1
-      w3 = prmt(v1, v2, 0x6030u);  // g2 g3
-      w4 = prmt(v0, v1, 0x5020u);  // b0 b1
-      w5 = prmt(v2, v2, 0x3000u);  // b2 b3
-      const int x = xs + 4 * q;
-      if (x < 0 || x + 3 >= W) {
-        uint32_t m0 = 0, m1 = 0;
-        if (x + 0 < 0 || x + 0 >= W) m0 |= 0x0000ff00u;
-        if (x + 1 < 0 || x + 1 >= W) m0 |= 0xff000000u;
-        if (x + 2 < 0 || x + 2 >= W) m1 |= 0x0000ff00u;
-        if (x + 3 < 0 || x + 3 >= W) m1 |= 0xff000000u;
-        w0 |= m0; w2 |= m0; w4 |= m0;
-        w1 |= m1; w3 |= m1; w5 |= m1;
-      }
-    }
-    uint32_t* r0 = pl + (0 * G::EH + e) * G::PLW + 2 * q;
-    uint32_t* r1 = pl + (1 * G::EH + e) * G::PLW + 2 * q;
-    uint32_t* r2 = pl + (2 * G::EH + e) * G::PLW + 2 * q;
-    r0[0] = w0; r0[1] = w1;
-    r1[0] = w2; r1[1] = w3;
-    r2[0] = w4; r2[1] = w5;
+  for (int i = tid; i < (G::NT / 32) * 256; i += G::NT) whist[i] = 0u;
+  if (tid == 0) {
+    s_fail = 0;
+    for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  p1_stage_band<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar);
+  __syncthreads();  // +inf fills visible
 
-  // ---- stage 3: vertical minimum over P rows, in place -----------------
-  for (int it = tid; it < 3 * G::EWW; it += P1_THREADS) {
-    const int c = it / G::EWW, w = it - c * G::EWW;
-    uint32_t* col = pl + (c * G::EH) * G::PLW + w;
-    uint32_t v[G::EH];
-#pragma unroll
-    for (int e = 0; e < G::EH; ++e) v[e] = col[e * G::PLW];
-    slide_min<G::EH, G::P>(v);
-#pragma unroll
-    for (int i = 0; i < P1_TH; ++i) col[i * G::PLW] = v[i];
-  }
-  __syncthreads();
-
-  // ---- stage 4: horizontal minimum on u16x2 pairs ----------------------
+  // ---- phase 1: vertical minima, in place, as the chunks land -----------
   {
-    constexpr int SEG = G::SEG;
-    constexpr int NA = SEG + R;          // a values needed
-    constexpr int NB = (R > 0) ? SEG + R - 1 : 1;
-    constexpr int NWL = SEG + R + 2;     // words loaded
-    constexpr int NS = G::POUT_W / SEG;  // items per row
-    for (int it = tid; it < 3 * P1_TH * NS; it += P1_THREADS) {
-      const int c = it / (P1_TH * NS);
-      const int rem = it - c * (P1_TH * NS);
-      const int i = rem / NS, s = rem - i * NS;
-      const uint32_t* row = pl + (c * G::EH + i) * G::PLW;
-      const int j0 = (G::E0 >> 1) + s * SEG;
-      uint32_t Wd[NWL];
-#pragma unroll
-      for (int k = 0; k < NWL; ++k) {
-        const int j = j0 + k;
-        Wd[k] = (j < G::EWW) ? row[j] : 0xffffffffu;
+    uint32_t hE[P], hO[P];
+    const int j = min(tid, G::NWC - 1);
+    const bool owner = tid < G::NWC;
+    int fail = 0;
+    for (int c = 0; c < G::NCH && !fail; ++c) {
+      if (!mbar_wait_bounded(mbar + c, 0u)) {
+        fail = 1;
+        break;
       }
-      uint32_t a[NA], b[NB];
-      if constexpr ((G::E0 & 1) == 0) {
+      if (owner) {
 #pragma unroll
-        for (int k = 0; k < NA; ++k) a[k] = Wd[k];
-        if constexpr (R > 0) {
-#pragma unroll
-          for (int k = 0; k < NB; ++k) b[k] = prmt(Wd[k], Wd[k + 1], 0x5432u);
+        for (int bb = 0; bb < G::NBLK; ++bb) {
+          const int B = c * G::NBLK + bb;
+          if (B < nblocks) p1_vblock<R>(smem, B, j, hE, hO);
         }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NA; ++k) a[k] = prmt(Wd[k], Wd[k + 1], 0x5432u);
-        if constexpr (R > 0) {
-#pragma unroll
-          for (int k = 0; k < NB; ++k) b[k] = Wd[k + 1];
-        }
-      }
-      slide_min<NA, R + 1>(a);
-      if constexpr (R > 0) slide_min<NB, (R > 0 ? R : 1)>(b);
-      uint32_t* o = pout + (c * P1_TH + i) * G::POUT_W + s * SEG;
-#pragma unroll
-      for (int k = 0; k < SEG; ++k) {
-        if constexpr (R > 0) o[k] = vmin2(a[k], b[k]);
-        else o[k] = a[k];
       }
     }
+    if (fail) s_fail = 1;
   }
   __syncthreads();
-
-  // ---- stage 5: D, histogram, tile maximum, P and optional D stores -----
-  unsigned tmax = 0;
-  const int wid = tid >> 5;
-  unsigned* hw = whist + wid * 256;
-  for (int it = tid; it < P1_TH * (P1_TW / 4); it += P1_THREADS) {
-    const int i = it / (P1_TW / 4), q = it - i * (P1_TW / 4);
-    const int y = y0 + i, x = x0 + 4 * q;
-    if (y >= H || x >= W) continue;
-    const uint32_t* pr = pout + (0 * P1_TH + i) * G::POUT_W + 2 * q;
-    const uint32_t* pg = pout + (1 * P1_TH + i) * G::POUT_W + 2 * q;
-    const uint32_t* pb = pout + (2 * P1_TH + i) * G::POUT_W + 2 * q;
-    const uint32_t R0 = pr[0], R1 = pr[1], G0 = pg[0], G1 = pg[1], B0 = pb[0], B1 = pb[1];
-    const uint32_t d0 = vmin2(vmin2(R0, G0), B0), d1 = vmin2(vmin2(R1, G1), B1);
-    const uint32_t dw = prmt(d0, d1, 0x7531u);  // D of the 4 pixels
-    // interleaved P bytes: [r0 g0 b0 r1] [g1 b1 r2 g2] [b2 r3 g3 b3]
-    const uint32_t t0 = prmt(R0, G0, 0x3051u);
-    const uint32_t o0 = prmt(t0, B0, 0x3510u);
-    const uint32_t t1 = prmt(G0, B0, 0x0073u), u1 = prmt(R1, G1, 0x5100u);
-    const uint32_t o1 = prmt(t1, u1, 0x7610u);
-    const uint32_t t2 = prmt(B1, R1, 0x0071u), u2 = prmt(G1, B1, 0x7300u);
-    const uint32_t o2 = prmt(t2, u2, 0x7610u);
-    uint32_t* Pp = reinterpret_cast<uint32_t*>(jb.P + (long long)y * jb.P_pitch + 3LL * x);
-    Pp[0] = o0; Pp[1] = o1; Pp[2] = o2;
-    const int nv = min(4, W - x);
-    if (jb.Dout) {
-      uint8_t* Dp = jb.Dout + (long long)y * jb.D_pitch + x;
-      for (int k = 0; k < nv; ++k) Dp[k] = uint8_t((dw >> (8 * k)) & 0xff);
-    }
-    unsigned cur = dw & 0xff, cnt = 1;
-    tmax = max(tmax, cur);
-    for (int k = 1; k < nv; ++k) {
-      const unsigned d = (dw >> (8 * k)) & 0xff;
-      tmax = max(tmax, d);
-      if (d == cur) {
-        ++cnt;
-      } else {
-        atomicAdd(&hw[cur], cnt);
-        cur = d;
-        cnt = 1;
-      }
-    }
-    atomicAdd(&hw[cur], cnt);
+  if (s_fail) {
+    for (int c = 0; c < G::NCH; ++c) (void)mbar_wait_bounded(mbar + c, 0u);
+    if (tid == 0) jb.rec->status = HZ_STATUS_DEVICE_TIMEOUT;
+    return;
   }
-  // tile maximum
+
+  // ---- phase 2: horizontal minima, (row, 64-pixel segment) per thread ----
+  unsigned tmax = 0;
+  unsigned* hw = whist + (tid >> 5) * 256;
+  for (int it = tid; it < bh * P1_NSEG; it += G::NT) {
+    const int seg = it / bh, k = it - seg * bh;
+    const int xo = x0 + seg * P1_HSEG;  // first output pixel
+    if (xo >= W) continue;
+    const uint4* vq = reinterpret_cast<const uint4*>(smem + k * G::SLOT + G::IB0 + 3 * P1_HSEG * seg);
+    const int sp0 = xo - R;  // image pixel of element 0
+    const bool edge = (sp0 < 0) || (sp0 + G::NIN > W);
+    uint4* Pp = reinterpret_cast<uint4*>(jb.P + (long long)(y0 + k) * jb.P_pitch + 3LL * xo);
+    uint8_t* Dp = jb.Dout ? jb.Dout + (long long)(y0 + k) * jb.D_pitch + xo : nullptr;
+    if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw, tmax);
+    else p1_hitem<R, false>(vq, sp0, W, P1_HSEG, Pp, nullptr, hw, tmax);
+  }
+  // region maximum and histogram
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-  if ((tid & 31) == 0) red[wid] = tmax;
+  if ((tid & 31) == 0) red[tid >> 5] = tmax;
   __syncthreads();
-  {
-    unsigned s = 0;
+  for (int bin = tid; bin < 256; bin += G::NT) {
+    unsigned sum = 0;
 #pragma unroll
-    for (int w = 0; w < P1_THREADS / 32; ++w) s += whist[w * 256 + tid];
-    if (s) atomicAdd(&jb.rec->hist[tid], s);
+    for (int w = 0; w < G::NT / 32; ++w) sum += whist[w * 256 + bin];
+    if (sum) atomicAdd(&jb.rec->hist[bin], sum);
   }
   if (tid == 0) {
     unsigned m = 0;
-#pragma unroll
-    for (int w = 0; w < P1_THREADS / 32; ++w) m = max(m, red[w]);
-    jb.tilemax[tile] = uint8_t(m);
+    for (int w = 0; w < G::NT / 32; ++w) m = max(m, red[w]);
+    jb.tilemax[item] = uint8_t(m);
   }
-  // ---- last tile of the frame: threshold level T (Eq. 3 set) -----------
   __threadfence();
   __syncthreads();
   if (tid == 0) {
-    const unsigned ntiles = unsigned(jb.tiles_x * jb.tiles_y);
-    s_last = (atomicAdd(&jb.rec->done_p1, 1u) == ntiles - 1u);
+    const unsigned nitems = unsigned(jb.tiles_x * jb.tiles_y);
+    s_last = (atomicAdd(&jb.rec->done_p1, 1u) == nitems - 1u);
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // suffix counts S(v) = #(D >= v); T = max{v : S(v) >= K}
-  const unsigned h = __ldcg(&jb.rec->hist[255 - tid]);
-  const unsigned incl = block_scan_incl(h, red, nullptr);
-  const unsigned excl = incl - h;
-  const unsigned long long K = (unsigned long long)jb.K;
-  if (incl >= K && excl < K) {
-    jb.rec->T = 255 - tid;
-    jb.rec->n_above = (long long)excl;
-    jb.rec->m_ties = (long long)(K - excl);
+  // suffix counts S(v) = #(D >= v); T = max{v : S(v) >= K}, scanned by the
+  // first 256 threads
+  const unsigned hv = (tid < 256) ? __ldcg(&jb.rec->hist[255 - tid]) : 0u;
+  unsigned h = hv;
+  const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, h, o);
+    if (lane >= o) h += t;
+  }
+  if (lane == 31 && wid < 8) red[wid] = h;
+  __syncthreads();
+  if (tid < 256) {
+    unsigned add = 0;
+    for (int w = 0; w < wid; ++w) add += red[w];
+    const unsigned incl = h + add, excl = incl - hv;
+    const unsigned long long K = (unsigned long long)jb.K;
+    if (incl >= K && excl < K) {
+      jb.rec->T = 255 - tid;
+      jb.rec->n_above = (long long)excl;
+      jb.rec->m_ties = (long long)(K - excl);
+    }
   }
 }
 
 template <int R>
-__global__ void __launch_bounds__(P1_THREADS) k_p1(const __grid_constant__ HzJobs jobs) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(P1S<R>::NT) k_p1(const __grid_constant__ HzJobs jobs) {
+  extern __shared__ __align__(128) unsigned char smem[];
   const HzJob& jb = jobs.j[blockIdx.y];
-  const int tile = blockIdx.x;
-  if (tile >= jb.tiles_x * jb.tiles_y) return;
-  p1_tile<R>(jb, tile, smem);
+  const int item = blockIdx.x;
+  if (item >= jb.tiles_x * jb.tiles_y) return;
+  p1_region<R>(jb, item, smem);
 }
 
 // ------------------------------------------------------------------------
@@ -429,28 +558,28 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
 
 __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   const HzJob& jb = jobs.j[blockIdx.y];
-  const int tile = blockIdx.x;
-  const int ntiles = jb.tiles_x * jb.tiles_y;
-  if (tile >= ntiles) return;
+  const int item = blockIdx.x;
+  const int nitems = jb.tiles_x * jb.tiles_y;
+  if (item >= nitems) return;
   __shared__ unsigned long long shl[8];
   __shared__ int s_last;
   const int tid = threadIdx.x;
   HzFrameRec* rec = jb.rec;
   const int T = rec->T;
-  if ((int)jb.tilemax[tile] >= T) {
-    const int tx = tile % jb.tiles_x, ty = tile / jb.tiles_x;
-    const int x0 = tx * P1_TW, y0 = ty * P1_TH;
+  if ((int)jb.tilemax[item] >= T) {
+    const int strip = item % jb.tiles_x, band = item / jb.tiles_x;
+    const int x0 = strip * P1_SW, y0 = band * jb.band_h;
     const int lane = tid & 31, wid = tid >> 5;
     unsigned ar = 0, ag = 0, ab = 0;
-    for (int i = wid; i < P1_TH; i += 8) {
+    for (int i = wid; i < jb.band_h; i += 8) {
       const int y = y0 + i;
       if (y >= jb.H) break;
-      const int x = x0 + 4 * lane;
       unsigned tr = 0, tg = 0, tb = 0, tc = 0;
-      if (x < jb.W) {
+      for (int xq = 0; xq < P1_SW; xq += 128) {
+        const int x = x0 + xq + 4 * lane;
+        if (xq + 4 * lane >= P1_SW || x >= jb.W) continue;
         const uint32_t* Pp = reinterpret_cast<const uint32_t*>(jb.P + (long long)y * jb.P_pitch + 3LL * x);
-        const uint32_t p0 = __ldcg(Pp), p1 = __ldcg(Pp + 1), p2 = __ldcg(Pp + 2);
-        const uint32_t bytes[3] = {p0, p1, p2};
+        const uint32_t bytes[3] = {__ldcg(Pp), __ldcg(Pp + 1), __ldcg(Pp + 2)};
         const int nv = min(4, jb.W - x);
         const uint8_t* Ip = jb.in + (long long)y * jb.in_pitch + 3LL * x;
         for (int k = 0; k < nv; ++k) {
@@ -495,7 +624,7 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(ntiles) - 1u);
+  if (tid == 0) s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
   __syncthreads();
   if (!s_last) return;
   __threadfence();

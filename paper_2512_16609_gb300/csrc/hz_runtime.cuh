@@ -85,17 +85,25 @@ inline hz_status fail(hz_ctx* c, hz_status s, const char* fmt, ...) {
                         __FILE__, __LINE__);                                            \
   } while (0)
 
+#define HZ_TRY(expr)              \
+  do {                            \
+    hz_status st_ = (expr);       \
+    if (st_ != HZ_OK) return st_; \
+  } while (0)
+
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Per-frame scratch plan.
 struct FramePlan {
-  int W, H, tiles_x, tiles_y, segs;
+  int W, H, tiles_x, tiles_y, segs, band_h;
   long long K;
   long long P_pitch;
   size_t off_rec, off_rowcnt, off_rowsum;  // in the zeroed region
   size_t off_P, off_tilemax, off_bal;      // in the rest
   size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
   long long plane_pitch32, plane_pitch16;
+  size_t off_copy;                          // aligned copy of an unaligned input (0 if none)
+  long long copy_pitch;
 };
 
 struct LaunchPlan {
@@ -114,21 +122,28 @@ inline long long num_top(long long N, float frac) {
 }
 
 // image: add the guided-filter planes
+// The dark-channel kernel stages rows with 16-byte bulk copies: an input
+// whose base or pitch is not a multiple of 16 is first copied into an
+// aligned buffer of the plan.
+inline bool input_aligned16(const void* p, size_t pitch) { return ((uintptr_t(p) | uintptr_t(pitch)) & 15) == 0; }
+
 inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int n, bool image, bool balance,
-                        LaunchPlan& lp) {
+                        LaunchPlan& lp, const hz_frame_desc* fr = nullptr) {
   lp.fp.resize(n);
-  size_t z = 0;
+  // zeroed region: the n records first (contiguous, one copy reads them
+  // back), then the per-row tie counts and sums
+  size_t z = align_up(sizeof(HzFrameRec) * size_t(n), 256);
   for (int i = 0; i < n; ++i) {
     FramePlan& f = lp.fp[i];
     f.W = Ws[i];
     f.H = Hs[i];
-    f.tiles_x = (f.W + P1_TW - 1) / P1_TW;
-    f.tiles_y = (f.H + P1_TH - 1) / P1_TH;
+    f.band_h = p1_band_rows(prm.patch / 2);
+    f.tiles_x = (f.W + P1_SW - 1) / P1_SW;
+    f.tiles_y = (f.H + f.band_h - 1) / f.band_h;
     f.segs = p3_units(f.W, f.H);
     f.K = num_top((long long)f.W * f.H, prm.top_fraction);
-    f.P_pitch = (long long)align_up(size_t(3) * P1_TW * f.tiles_x, 128);
-    f.off_rec = z;
-    z = align_up(z + sizeof(HzFrameRec), 256);
+    f.P_pitch = (long long)align_up(size_t(3) * P1_SW * f.tiles_x, 128);
+    f.off_rec = sizeof(HzFrameRec) * size_t(i);
     f.off_rowcnt = z;
     z = align_up(z + sizeof(unsigned) * f.H, 256);
     f.off_rowsum = z;
@@ -146,6 +161,13 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     if (balance) {
       f.off_bal = o;
       o = align_up(o + sizeof(double) * 3 * size_t(f.segs), 256);
+    }
+    f.off_copy = 0;
+    f.copy_pitch = 0;
+    if (fr && !input_aligned16(fr[i].in, fr[i].in_pitch)) {
+      f.copy_pitch = (long long)align_up(size_t(3) * f.W, 16);
+      f.off_copy = o;
+      o = align_up(o + size_t(f.copy_pitch) * f.H, 1024);
     }
     f.off_t = f.off_vs = f.off_a = f.off_b = f.off_q = 0;
     f.plane_pitch32 = (long long)align_up(size_t(4) * f.W, 128);
@@ -202,6 +224,8 @@ struct LaunchScope {
 };
 
 hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s);
+// Copies of unaligned inputs into the plan's aligned buffers (scratch base).
+cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base, cudaStream_t s);
 hz_status set_p1_attributes(hz_ctx* c);
 HzKParams kparams_of(const hz_params& p);
 hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& jobs);
@@ -217,6 +241,11 @@ hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool bal
 hz_status run_image_job(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s);
 // Copy records back (waits for the stream) and fill infos.
 hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_frame_info* infos, bool balance);
+void recs_to_infos(const HzFrameRec* recs, const LaunchPlan& lp, int n, hz_frame_info* infos, bool balance);
+
+// Mixed batch of frames (plain batched, guided one by one), see hz_api.cu.
+hz_status run_batch(hz_ctx* c, const hz_frame_desc* frames, int n, cudaStream_t s, hz_frame_info* infos,
+                    HzFrameRec* rec_sink, int* order);
 
 // serving (hz_server.cu)
 void server_stop(hz_ctx* c);

@@ -9,7 +9,278 @@
 
 namespace hz {
 
-void server_stop(hz_ctx*) {}
+using Clock = std::chrono::steady_clock;
+
+static double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t ticket;
+  int sid;
+  const uint8_t* in;
+  size_t in_pitch;
+  uint8_t* out;
+  size_t out_pitch;
+  uint32_t flags;
+  int W, H;
+  double t_submit;
+};
+
+struct DoneRec {
+  hz_status st;
+  hz_frame_info info;
+};
+
+constexpr int NSLOT = 3;     // batches in flight
+constexpr int MAX_BATCH = 64;
+
+struct Slot {
+  Arena stage;                      // device staging of host-IO frames
+  HzFrameRec* recs = nullptr;       // pinned records, processing order
+  int order[MAX_BATCH];
+  std::vector<Request> reqs;
+  cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr, ev_done = nullptr;
+  hz_status st = HZ_OK;
+  bool busy = false;
+};
+
+struct Server {
+  hz_ctx* c = nullptr;
+  std::thread sched, compl_th;
+  std::mutex mu;
+  std::condition_variable cv_req, cv_done, cv_slot, cv_inflight;
+  std::deque<Request> pending;
+  std::map<uint64_t, DoneRec> done;
+  std::deque<int> inflight;         // slots in launch order
+  uint64_t next_ticket = 1;
+  size_t outstanding[MAX_STREAMS] = {0};
+  bool stop = false;
+  cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+  Slot slot[NSLOT];
+  std::vector<double> lat_ms;
+  uint64_t batches = 0, frames = 0;
+  double t_first = -1.0, t_last = 0.0;
+};
+
+static void complete_loop(Server* S) {
+  hz_ctx* c = S->c;
+  cudaSetDevice(c->device);
+  for (;;) {
+    int si;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_inflight.wait(lk, [&] { return S->stop || !S->inflight.empty(); });
+      if (S->inflight.empty()) return;
+      si = S->inflight.front();
+    }
+    Slot& sl = S->slot[si];
+    hz_status st = sl.st;
+    if (st == HZ_OK && cudaEventSynchronize(sl.ev_done) != cudaSuccess) {
+      cudaGetLastError();
+      st = HZ_ECUDA;
+    }
+    const double t = now_s();
+    const bool bal = c->prm.color_balance != 0;
+    const int n = (int)sl.reqs.size();
+    std::vector<hz_frame_info> infos(n);
+    if (st == HZ_OK) {
+      for (int k = 0; k < n; ++k) {
+        const int i = sl.order[k];
+        const Request& r = sl.reqs[i];
+        LaunchPlan lp;
+        plan_frames(c->prm, &r.W, &r.H, 1, false, false, lp);
+        recs_to_infos(sl.recs + k, lp, 1, &infos[i], bal);
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (int i = 0; i < n; ++i) {
+        const Request& r = sl.reqs[i];
+        hz_status fs = st;
+        if (fs == HZ_OK && infos[i].status != 0) fs = HZ_EDEVICE_TIMEOUT;
+        S->done[r.ticket] = DoneRec{fs, infos[i]};
+        S->lat_ms.push_back(1e3 * (t - r.t_submit));
+        if (S->outstanding[r.sid]) --S->outstanding[r.sid];
+      }
+      S->frames += n;
+      S->t_last = t;
+      sl.reqs.clear();
+      sl.busy = false;
+      S->inflight.pop_front();
+    }
+    S->cv_done.notify_all();
+    S->cv_slot.notify_all();
+  }
+}
+
+// Enqueue one batch on the slot: H2D of host frames, the batched launch,
+// D2H of host outputs and of the records. Returns the launch status.
+static hz_status launch_batch(Server* S, Slot& sl) {
+  hz_ctx* c = S->c;
+  const int n = (int)sl.reqs.size();
+  size_t need = 0;
+  for (const Request& r : sl.reqs)
+    if (r.flags & HZ_IO_HOST) need += 2 * align_up(size_t(3) * r.W * r.H, 256);
+  if (need > sl.stage.cap) {
+    if (sl.stage.base) cudaFree(sl.stage.base);
+    sl.stage.base = nullptr;
+    sl.stage.cap = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HZ_ENOMEM, "server staging of %zu bytes failed", need);
+    }
+    sl.stage.base = static_cast<uint8_t*>(p);
+    sl.stage.cap = need;
+  }
+  std::vector<hz_frame_desc> fr(n);
+  size_t o = 0;
+  bool any_host = false;
+  for (int i = 0; i < n; ++i) {
+    const Request& r = sl.reqs[i];
+    fr[i] = hz_frame_desc{r.in, r.in_pitch, r.out, r.out_pitch, r.W, r.H, r.sid,
+                          c->stream_flags[r.sid] & HZ_GUIDED};
+    if (r.flags & HZ_IO_HOST) {
+      any_host = true;
+      const size_t fb = align_up(size_t(3) * r.W * r.H, 256);
+      uint8_t* din = sl.stage.base + o;
+      uint8_t* dout = din + fb;
+      o += 2 * fb;
+      HZ_CK(c, cudaMemcpy2DAsync(din, size_t(3) * r.W, r.in, r.in_pitch, size_t(3) * r.W, r.H,
+                                 cudaMemcpyHostToDevice, S->s_h2d));
+      fr[i].in = din;
+      fr[i].in_pitch = size_t(3) * r.W;
+      fr[i].out = dout;
+      fr[i].out_pitch = size_t(3) * r.W;
+    }
+  }
+  HZ_CK(c, cudaEventRecord(sl.ev_h2d, S->s_h2d));
+  HZ_CK(c, cudaStreamWaitEvent(S->s_comp, sl.ev_h2d, 0));
+  {
+    std::lock_guard<std::mutex> lk(c->call_mu);
+    cudaSetDevice(c->device);
+    HZ_TRY(order_after_previous(c, S->s_comp));
+    HZ_TRY(run_batch(c, fr.data(), n, S->s_comp, nullptr, sl.recs, sl.order));
+    HZ_TRY(mark_done(c, S->s_comp));
+  }
+  HZ_CK(c, cudaEventRecord(sl.ev_comp, S->s_comp));
+  HZ_CK(c, cudaStreamWaitEvent(S->s_d2h, sl.ev_comp, 0));
+  if (any_host) {
+    for (int i = 0; i < n; ++i) {
+      const Request& r = sl.reqs[i];
+      if (!(r.flags & HZ_IO_HOST)) continue;
+      HZ_CK(c, cudaMemcpy2DAsync(r.out, r.out_pitch, fr[i].out, fr[i].out_pitch, size_t(3) * r.W, r.H,
+                                 cudaMemcpyDeviceToHost, S->s_d2h));
+    }
+  }
+  HZ_CK(c, cudaEventRecord(sl.ev_done, S->s_d2h));
+  return HZ_OK;
+}
+
+static void schedule_loop(Server* S) {
+  hz_ctx* c = S->c;
+  cudaSetDevice(c->device);
+  for (;;) {
+    int si = -1;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_req.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop) return;
+      S->cv_slot.wait(lk, [&] {
+        if (S->stop) return true;
+        for (int k = 0; k < NSLOT; ++k)
+          if (!S->slot[k].busy) return true;
+        return false;
+      });
+      if (S->stop) return;
+      for (int k = 0; k < NSLOT; ++k)
+        if (!S->slot[k].busy) {
+          si = k;
+          break;
+        }
+      // continuous batching: the oldest pending frame of every stream joins
+      // this batch; later frames of a stream wait for the next one
+      Slot& sl = S->slot[si];
+      sl.reqs.clear();
+      bool taken[MAX_STREAMS] = {false};
+      for (auto it = S->pending.begin(); it != S->pending.end() && (int)sl.reqs.size() < MAX_BATCH;) {
+        if (taken[it->sid]) {
+          ++it;
+          continue;
+        }
+        taken[it->sid] = true;
+        sl.reqs.push_back(*it);
+        it = S->pending.erase(it);
+      }
+      sl.busy = true;
+    }
+    Slot& sl = S->slot[si];
+    sl.st = launch_batch(S, sl);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->batches += 1;
+      S->inflight.push_back(si);
+    }
+    S->cv_inflight.notify_all();
+  }
+}
+
+static hz_status server_start(hz_ctx* c) {
+  if (c->server) return HZ_OK;
+  Server* S = new (std::nothrow) Server();
+  if (!S) return HZ_ENOMEM;
+  S->c = c;
+  bool ok = cudaStreamCreateWithFlags(&S->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; ok && k < NSLOT; ++k) {
+    Slot& sl = S->slot[k];
+    ok = cudaMallocHost(&sl.recs, sizeof(HzFrameRec) * MAX_BATCH) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sl.ev_comp, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming | cudaEventBlockingSync) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    c->server = S;
+    server_stop(c);
+    return fail(c, HZ_ECUDA, "server start failed");
+  }
+  c->server = S;
+  S->sched = std::thread(schedule_loop, S);
+  S->compl_th = std::thread(complete_loop, S);
+  return HZ_OK;
+}
+
+void server_stop(hz_ctx* c) {
+  Server* S = c->server;
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_req.notify_all();
+  S->cv_slot.notify_all();
+  if (S->sched.joinable()) S->sched.join();
+  // the completion thread drains the batches already launched
+  S->cv_inflight.notify_all();
+  if (S->compl_th.joinable()) S->compl_th.join();
+  for (int k = 0; k < NSLOT; ++k) {
+    Slot& sl = S->slot[k];
+    if (sl.stage.base) cudaFree(sl.stage.base);
+    if (sl.recs) cudaFreeHost(sl.recs);
+    if (sl.ev_h2d) cudaEventDestroy(sl.ev_h2d);
+    if (sl.ev_comp) cudaEventDestroy(sl.ev_comp);
+    if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+  }
+  if (S->s_comp) cudaStreamDestroy(S->s_comp);
+  if (S->s_h2d) cudaStreamDestroy(S->s_h2d);
+  if (S->s_d2h) cudaStreamDestroy(S->s_d2h);
+  cudaGetLastError();
+  delete S;
+  c->server = nullptr;
+}
 
 }  // namespace hz
 
@@ -59,6 +330,10 @@ extern "C" hz_status hz_close_stream(hz_ctx* c, int32_t sid) {
   if (!c) return HZ_EINVAL;
   std::lock_guard<std::mutex> lk(c->smu);
   if (sid < 0 || sid >= MAX_STREAMS || !c->stream_open[sid]) return fail(c, HZ_EINVAL, "stream %d is not open", sid);
+  if (c->server) {
+    std::lock_guard<std::mutex> lk2(c->server->mu);
+    if (c->server->outstanding[sid]) return fail(c, HZ_ESTATE, "stream %d has frames in flight", sid);
+  }
   c->stream_open[sid] = 0;
   c->resident_bytes -= c->stream_bytes[sid];
   c->stream_bytes[sid] = 0;
@@ -96,17 +371,103 @@ extern "C" hz_status hz_stream_set_state(hz_ctx* c, int32_t sid, const void* buf
   return HZ_OK;
 }
 
-extern "C" hz_status hz_submit(hz_ctx* c, int32_t, const uint8_t*, size_t, uint8_t*, size_t, uint32_t,
-                               uint64_t*) {
-  return c ? fail(c, HZ_ESTATE, "scheduler not started") : HZ_EINVAL;
+extern "C" hz_status hz_submit(hz_ctx* c, int32_t sid, const uint8_t* in, size_t in_pitch, uint8_t* out,
+                               size_t out_pitch, uint32_t flags, uint64_t* ticket) {
+  if (!c || !ticket) return HZ_EINVAL;
+  if (flags & ~uint32_t(HZ_IO_HOST)) return fail(c, HZ_EINVAL, "unknown submit flags");
+  int W, H;
+  {
+    std::lock_guard<std::mutex> lk(c->smu);
+    if (sid < 0 || sid >= MAX_STREAMS || !c->stream_open[sid]) return fail(c, HZ_EINVAL, "stream %d is not open", sid);
+    W = c->stream_W[sid];
+    H = c->stream_H[sid];
+  }
+  if (!in || !out || in_pitch < size_t(3) * W || out_pitch < size_t(3) * W)
+    return fail(c, HZ_EINVAL, "bad buffers for a %dx%d stream", W, H);
+  {
+    std::lock_guard<std::mutex> lk(c->smu);
+    if (!c->server) {
+      hz_status st = server_start(c);
+      if (st != HZ_OK) return st;
+    }
+  }
+  Server* S = c->server;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return fail(c, HZ_ESTATE, "server stopped");
+    const double t = now_s();
+    if (S->t_first < 0) S->t_first = t;
+    Request r{S->next_ticket++, sid, in, in_pitch, out, out_pitch, flags, W, H, t};
+    *ticket = r.ticket;
+    S->pending.push_back(r);
+    S->outstanding[sid] += 1;
+  }
+  S->cv_req.notify_one();
+  return HZ_OK;
 }
 
-extern "C" hz_status hz_poll(hz_ctx* c, uint64_t, int64_t, hz_frame_info*) {
-  return c ? fail(c, HZ_ESTATE, "scheduler not started") : HZ_EINVAL;
+extern "C" hz_status hz_poll(hz_ctx* c, uint64_t ticket, int64_t timeout_us, hz_frame_info* info) {
+  if (!c) return HZ_EINVAL;
+  Server* S = c->server;
+  if (!S) return fail(c, HZ_EINVAL, "no ticket %llu", (unsigned long long)ticket);
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (ticket == 0 || ticket >= S->next_ticket) return fail(c, HZ_EINVAL, "no ticket %llu", (unsigned long long)ticket);
+  auto ready = [&] { return S->done.count(ticket) != 0; };
+  if (!ready()) {
+    bool known = false;
+    for (const Request& r : S->pending) known |= (r.ticket == ticket);
+    for (int k = 0; k < NSLOT && !known; ++k)
+      for (const Request& r : S->slot[k].reqs) known |= (r.ticket == ticket);
+    if (!known) return fail(c, HZ_EINVAL, "ticket %llu was already collected", (unsigned long long)ticket);
+    if (timeout_us == 0) return HZ_EAGAIN;
+    if (timeout_us < 0) {
+      S->cv_done.wait(lk, ready);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
+      return HZ_ETIMEDOUT;
+    }
+  }
+  DoneRec d = S->done[ticket];
+  S->done.erase(ticket);
+  if (info) *info = d.info;
+  if (d.st != HZ_OK) return fail(c, d.st, "frame of ticket %llu failed", (unsigned long long)ticket);
+  return HZ_OK;
 }
 
 extern "C" hz_status hz_get_server_stats(hz_ctx* c, hz_server_stats* out) {
   if (!c || !out) return HZ_EINVAL;
   std::memset(out, 0, sizeof *out);
+  Server* S = c->server;
+  if (!S) return HZ_OK;
+  std::vector<double> lat;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    lat = S->lat_ms;
+    out->frames_done = S->frames;
+    out->batches = S->batches;
+    out->busy_s = (S->t_first >= 0) ? S->t_last - S->t_first : 0.0;
+  }
+  if (!lat.empty()) {
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double q) { return lat[std::min(lat.size() - 1, size_t(q * (lat.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    double sum = 0.0;
+    for (double v : lat) sum += v;
+    out->mean_ms = sum / double(lat.size());
+    out->max_ms = lat.back();
+  }
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_reset_server_stats(hz_ctx* c) {
+  if (!c) return HZ_EINVAL;
+  Server* S = c->server;
+  if (!S) return HZ_OK;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->lat_ms.clear();
+  S->frames = 0;
+  S->batches = 0;
+  S->t_first = -1.0;
+  S->t_last = 0.0;
   return HZ_OK;
 }
