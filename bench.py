@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="length of the served-streams measurement (0 skips it)")
     ap.add_argument("--frames", type=int, default=300,
                     help="frames per step; only profiling runs change it from the 300-frame workload")
     args = ap.parse_args()
@@ -196,6 +198,9 @@ def main():
     ws, rank, local = dist_env()
     nproc = max(1, min(16, (os.cpu_count() or 2) // max(ws, 1)))
     frames_np = make_inputs(nproc)
+    served_inputs = None
+    if args.served_seconds > 0 and rank == 0 and ws == 1:
+        served_inputs = make_served_inputs(nproc)
 
     import torch
     import __graft_entry__ as G
@@ -279,6 +284,10 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(hzp, ctx, frames_np, out, dev, args.steps, ws, barrier)
 
+    served = None
+    if served_inputs is not None:
+        served = run_served(hzp, dev, served_inputs, args.served_seconds)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_sample = 8
@@ -289,11 +298,116 @@ def main():
     hzp.hz_destroy(ctx)
     if rank == 0:
         emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-             launches, clocks)
+             launches, clocks, served)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+SERVED_MIX = [(1280, 720, 12, False), (1920, 1080, 12, False), (3840, 2160, 8, True)]
+SERVED_FPS = 30.0
+SERVED_FRAMES = 4  # distinct frames cycled by each stream
+
+
+def _served_frames(args):
+    W, H, seed = args
+    scene = hazegen.make_scene(W, H, seed)
+    return [hazegen.render(scene, hazegen.sequence_beta(f, SERVED_FRAMES), f) for f in range(SERVED_FRAMES)]
+
+
+def make_served_inputs(nproc):
+    specs = [(W, H, 1000 + k) for k, (W, H, _, _) in enumerate(SERVED_MIX)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(nproc, len(specs))) as pool:
+        return pool.map(_served_frames, specs)
+
+
+def arrivals(seconds, seed=7):
+    """(time, stream index) of Poisson arrivals at SERVED_FPS per stream."""
+    g = np.random.default_rng(seed)
+    ev = []
+    k = 0
+    for (W, H, n, guided) in SERVED_MIX:
+        for _ in range(n):
+            t = g.exponential(1.0 / SERVED_FPS)
+            while t < seconds:
+                ev.append((t, k))
+                t += g.exponential(1.0 / SERVED_FPS)
+            k += 1
+    ev.sort()
+    return ev
+
+
+def run_served(hzp, dev, frames_by_res, seconds):
+    """Served streams through hz_submit/hz_poll vs the plain per-frame path,
+    same arrivals; host (pinned) input and output buffers."""
+    import torch
+    prm = hzp.params(airlight_ema=0.9, precision="fp16", gf_radius=60)
+    kinds = []
+    for r, (W, H, n, guided) in enumerate(SERVED_MIX):
+        kinds += [(r, W, H, guided)] * n
+    host_in = [[torch.from_numpy(f).pin_memory() for f in frames_by_res[r]] for r in range(len(SERVED_MIX))]
+    ev = arrivals(seconds)
+    # ---- served ----
+    ctx = hzp.hz_create(prm, dev.index or 0)
+    sids = [hzp.hz_open_stream(ctx, W, H, hzp.HZ_GUIDED if g else 0) for (_, W, H, g) in kinds]
+    outs = [torch.empty_like(host_in[r][0]).pin_memory() for (r, _, _, _) in kinds]
+    # warm-up: one frame per stream
+    tks = [hzp.hz_submit(ctx, sids[k], host_in[kinds[k][0]][0], outs[k], hzp.HZ_IO_HOST) for k in range(len(kinds))]
+    for t in tks:
+        hzp.hz_poll(ctx, t, -1)
+    hzp.hz_reset_server_stats(ctx)
+    counts = [0] * len(kinds)
+    tickets = []
+    t0 = time.perf_counter()
+    for (ta, k) in ev:
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        r = kinds[k][0]
+        tickets.append(hzp.hz_submit(ctx, sids[k], host_in[r][counts[k] % SERVED_FRAMES], outs[k], hzp.HZ_IO_HOST))
+        counts[k] += 1
+    for t in tickets:
+        hzp.hz_poll(ctx, t, -1)
+    wall = time.perf_counter() - t0
+    st = hzp.hz_get_server_stats(ctx)
+    served = {"frames": int(st.frames_done), "batches": int(st.batches), "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+              "mean_ms": st.mean_ms, "max_ms": st.max_ms, "frames_per_s": st.frames_done / wall}
+    hzp.hz_destroy(ctx)
+    # ---- plain per-frame path: FIFO, one call per frame, host copies ----
+    ctx = hzp.hz_create(prm, dev.index or 0)
+    sids = [hzp.hz_open_stream(ctx, W, H) for (_, W, H, g) in kinds]
+    dbuf = {r: (torch.empty_like(host_in[r][0], device=dev), torch.empty_like(host_in[r][0], device=dev))
+            for r in range(len(SERVED_MIX))}
+    stream = torch.cuda.current_stream(dev)
+    lat = []
+    counts = [0] * len(kinds)
+    t0 = time.perf_counter()
+    for (ta, k) in ev:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        r, W, H, guided = kinds[k]
+        din, dout = dbuf[r]
+        din.copy_(host_in[r][counts[k] % SERVED_FRAMES], non_blocking=True)
+        if guided:
+            hzp.hz_dehaze_image(ctx, din, dout, stream=stream)
+        else:
+            hzp.hz_dehaze_frame(ctx, din, dout, stream_id=sids[k], stream=stream)
+        outs[k].copy_(dout, non_blocking=True)
+        stream.synchronize()
+        counts[k] += 1
+        lat.append(1e3 * (time.perf_counter() - t0 - ta))
+    wall = time.perf_counter() - t0
+    hzp.hz_destroy(ctx)
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
+    plain = {"frames": len(lat), "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": sum(lat) / len(lat),
+             "max_ms": lat[-1], "frames_per_s": len(lat) / wall}
+    return {"workload": "32 streams: 12x1280x720 + 12x1920x1080 video, 8x3840x2160 guided FP16 (r 60), "
+                        f"Poisson {SERVED_FPS:.0f} fps each, {seconds:.0f} s, pinned host I/O",
+            "served": served, "plain_fifo": plain}
 
 
 def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
@@ -317,7 +431,7 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
 
 
 def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-         launches, clocks):
+         launches, clocks, served=None):
     if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -338,6 +452,7 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
+            "serving": served,
         }
         print(json.dumps(line), flush=True)
 
