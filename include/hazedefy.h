@@ -284,6 +284,20 @@ hz_status hz_set_profiling(hz_ctx* ctx, int on);
  * copy them to *out and, if reset != 0, clear them. */
 hz_status hz_get_profile(hz_ctx* ctx, hz_profile* out, int reset);
 
+/* ------------------------------------------------------------ tuning -- */
+/* Wave size of the video path (the paper has no counterpart: it processes
+ * one frame at a time). hz_dehaze_video, hz_dehaze_batch and the server
+ * process frames in waves of at most 64 frames and about `bytes` of input
+ * (at least one frame per wave). A wave's input and per-channel patch
+ * minima stay resident in L2 between its dark-channel and reconstruction
+ * passes; a call with several waves runs them through a three-stage pipeline
+ * on streams of the context (dark channel of one wave, selection of the
+ * previous one, reconstruction of the one before), which the call's stream
+ * waits for. Results do not depend on the wave size. bytes = 0 restores the
+ * default (20 MiB). Must not race a dehaze call on the same context. */
+hz_status hz_set_wave_bytes(hz_ctx* ctx, size_t bytes);
+hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
+
 /* --------------------------------------------- allocation-free frame -- */
 /* The paper has no counterpart to this call; it exists for callers that are
  * not allowed to allocate device memory at run time: plug-ins that run inside

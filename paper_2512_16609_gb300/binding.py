@@ -142,6 +142,8 @@ _SIGS = {
     "hz_dehaze_frame_noalloc": (C.c_int, [C.POINTER(hz_params), _P, _I, _I, _SZ, _P, _SZ, _P, C.c_char_p, _SZ]),
     "hz_reset_server_stats": (C.c_int, [_P]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
+    "hz_set_wave_bytes": (C.c_int, [_P, _SZ]),
+    "hz_get_wave_bytes": (C.c_int, [_P, C.POINTER(_SZ)]),
     "hz_get_profile": (C.c_int, [_P, C.POINTER(hz_profile), C.c_int]),
 }
 
@@ -410,6 +412,17 @@ def params(**kw) -> hz_params:
         else:
             setattr(p, k, type(getattr(p, k))(v) if not isinstance(getattr(p, k), C.Array) else v)
     return p
+
+
+def hz_set_wave_bytes(ctx, nbytes: int):
+    """Input bytes per wave of the video path (0 = default)."""
+    return _check(lib().hz_set_wave_bytes(ctx, int(nbytes)), ctx, "hz_set_wave_bytes")
+
+
+def hz_get_wave_bytes(ctx) -> int:
+    v = _SZ(0)
+    _check(lib().hz_get_wave_bytes(ctx, C.byref(v)), ctx, "hz_get_wave_bytes")
+    return int(v.value)
 
 
 def hz_set_profiling(ctx, on: bool):

@@ -89,9 +89,10 @@ hz_status mark_done(hz_ctx* c, cudaStream_t s) {
   return HZ_OK;
 }
 
-void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video) {
+void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video,
+               uint8_t* base) {
   jobs.n = n;
-  uint8_t* A = c->arena.base;
+  uint8_t* A = base ? base : c->arena.base;
   for (int i = 0; i < n; ++i) {
     const FramePlan& f = lp.fp[i];
     HzJob& j = jobs.j[i];
@@ -113,6 +114,7 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.Dout = nullptr;
     j.D_pitch = 0;
     j.tilemax = A + f.off_tilemax;
+    j.rowmax = A + f.off_rowmax;
     j.rowcnt = reinterpret_cast<unsigned*>(A + f.off_rowcnt);
     j.rowsum = reinterpret_cast<unsigned*>(A + f.off_rowsum);
     j.rec = reinterpret_cast<HzFrameRec*>(A + f.off_rec);
@@ -157,13 +159,9 @@ static hz_status run_front(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, cudaSt
   hz_status st = launch_p1(c, c->prm.patch / 2, g1, s, jobs);
   if (st != HZ_OK) return st;
   {
+    // selection; its last block also runs the airlight chain
     LaunchScope ls(c, HZ_K_SELECT, s);
     k_p2<<<g1, 256, 0, s>>>(jobs, kp);
-  }
-  HZ_CK(c, cudaGetLastError());
-  {
-    LaunchScope ls(c, HZ_K_AIRLIGHT, s);
-    k_fin<<<1, FIN_THREADS, 0, s>>>(jobs, kp);
   }
   HZ_CK(c, cudaGetLastError());
   return HZ_OK;
@@ -400,6 +398,18 @@ extern "C" hz_status hz_create(const hz_params* p, int device, size_t mem_budget
             cudaEventCreateWithFlags(&c->done_ev, cudaEventDisableTiming) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking) == cudaSuccess;
+  int prio_lo = 0, prio_hi = 0;
+  if (ok) ok = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) == cudaSuccess;
+  // later pipeline stages first: they free the slots the earlier ones wait for
+  const int prio[3] = {prio_lo, (prio_lo + prio_hi) / 2, prio_hi};
+  for (int q = 0; ok && q < 3; ++q)
+    ok = cudaStreamCreateWithPriority(&c->ps[q], cudaStreamNonBlocking, prio[q]) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_dark[q], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_sel[q], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_free[q], cudaEventDisableTiming) == cudaSuccess;
+  if (ok)
+    ok = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < 2; ++i)
     ok = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
@@ -434,6 +444,15 @@ extern "C" hz_status hz_destroy(hz_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (int q = 0; q < 3; ++q) {
+    if (c->ps[q]) cudaStreamDestroy(c->ps[q]);
+    if (c->ev_dark[q]) cudaEventDestroy(c->ev_dark[q]);
+    if (c->ev_sel[q]) cudaEventDestroy(c->ev_sel[q]);
+    if (c->ev_free[q]) cudaEventDestroy(c->ev_free[q]);
+  }
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  if (c->ev_end) cudaEventDestroy(c->ev_end);
+  if (c->rec_pinned) cudaFreeHost(c->rec_pinned);
   if (c->copy_in) cudaStreamDestroy(c->copy_in);
   if (c->copy_out) cudaStreamDestroy(c->copy_out);
   cudaGetLastError();
@@ -480,43 +499,142 @@ static hz_status check_stream_id(hz_ctx* c, int32_t sid) {
   return HZ_OK;
 }
 
-// Video frames on device memory, chunked by MAXJ and an L2-sized wave.
-static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
-                              HzStreamState* chain, HzFrameRec* rec_sink = nullptr) {
-  const bool bal = c->prm.color_balance != 0;
-  const int tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+// Pinned host records for the pipelined path (grows; only touched by calls
+// that synchronise before returning, so nothing is in flight when it grows).
+static hz_status pinned_reserve(hz_ctx* c, size_t n) {
+  if (n <= c->rec_pinned_cap) return HZ_OK;
+  if (c->rec_pinned) cudaFreeHost(c->rec_pinned);
+  c->rec_pinned = nullptr;
+  c->rec_pinned_cap = 0;
+  const size_t want = std::max<size_t>(n, 256);
+  HZ_CK(c, cudaMallocHost(&c->rec_pinned, sizeof(HzFrameRec) * want));
+  c->rec_pinned_cap = want;
+  return HZ_OK;
+}
+
+// Waves of the frames: up to MAXJ frames and about c->wave_bytes of input
+// each (a wave's input and P stay L2-resident between its dark-channel and
+// reconstruction passes). wave_start gets the first frame of every wave and n.
+static void split_waves(const hz_ctx* c, const hz_frame_desc* fr, int n, std::vector<int>& wave_start) {
+  wave_start.clear();
   int i = 0;
   while (i < n) {
-    // frames per launch: up to MAXJ, and about 48 MB of input per wave so the
-    // second read of each frame is served from L2
+    wave_start.push_back(i);
     size_t bytes = 0;
     int m = 0;
     while (i + m < n && m < MAXJ) {
       const size_t fb = size_t(3) * fr[i + m].W * fr[i + m].H;
-      if (m > 0 && bytes + fb > (size_t(48) << 20)) break;
+      if (m > 0 && bytes + fb > c->wave_bytes) break;
       bytes += fb;
       ++m;
     }
-    std::vector<int> Ws(m), Hs(m);
-    for (int k = 0; k < m; ++k) {
-      Ws[k] = fr[i + k].W;
-      Hs[k] = fr[i + k].H;
-    }
-    LaunchPlan lp;
-    plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp, fr + i);
-    HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
-    HZ_CK(c, copy_unaligned(lp, fr + i, m, c->arena.base, s));
-    HzJobs jobs;
-    fill_jobs(c, lp, fr + i, m, jobs, tsrc);
-    if (chain)
-      for (int k = 0; k < m; ++k) jobs.j[k].state = chain;
-    HZ_TRY(run_video_jobs(c, lp, jobs, bal, s));
-    if (rec_sink)
-      HZ_CK(c, cudaMemcpyAsync(rec_sink + i, c->arena.base, sizeof(HzFrameRec) * size_t(m), cudaMemcpyDeviceToHost, s));
-    HZ_TRY(read_infos(c, lp, m, s, infos ? infos + i : nullptr, bal));
     i += m;
   }
+  wave_start.push_back(n);
+}
+
+static void wave_plan(hz_ctx* c, const hz_frame_desc* fr, int i, int m, bool bal, LaunchPlan& lp) {
+  std::vector<int> Ws(m), Hs(m);
+  for (int k = 0; k < m; ++k) {
+    Ws[k] = fr[i + k].W;
+    Hs[k] = fr[i + k].H;
+  }
+  plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp, fr + i);
+}
+
+// Several waves: a three-stage pipeline on the context's streams. The dark
+// channel of wave w (ps[0]), the selection and airlight chain of an earlier
+// wave (ps[1]) and the reconstruction of an earlier one still (ps[2]) run
+// concurrently; wave w owns arena slot w % PIPE_SLOTS from its zeroing to
+// the end of its reconstruction. Every selection runs on ps[1] in wave
+// order, so the airlight smoothing chain sees the frames in order.
+constexpr int PIPE_SLOTS = 3;
+
+static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::vector<int>& ws, cudaStream_t s,
+                                 hz_frame_info* infos, HzStreamState* chain, HzFrameRec* rec_sink) {
+  const bool bal = c->prm.color_balance != 0;
+  const int tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  const int nw = (int)ws.size() - 1, n = ws[nw];
+  std::vector<LaunchPlan> lps(nw);
+  size_t slot_bytes[PIPE_SLOTS] = {0, 0, 0};
+  for (int w = 0; w < nw; ++w) {
+    wave_plan(c, fr, ws[w], ws[w + 1] - ws[w], bal, lps[w]);
+    slot_bytes[w % PIPE_SLOTS] = std::max(slot_bytes[w % PIPE_SLOTS], align_up(lps[w].total, 4096));
+  }
+  size_t slot_off[PIPE_SLOTS], total = 0;
+  for (int k = 0; k < PIPE_SLOTS; ++k) {
+    slot_off[k] = total;
+    total += slot_bytes[k];
+  }
+  HZ_TRY(arena_reserve(c, c->arena, total, s));
+  HzFrameRec* recs = rec_sink;
+  if (!recs && infos) {
+    HZ_TRY(pinned_reserve(c, size_t(n)));
+    recs = c->rec_pinned;
+  }
+  const HzKParams kp = kparams_of(c->prm);
+  cudaStream_t sa = c->ps[0], sb = c->ps[1], sc = c->ps[2];
+  HZ_CK(c, cudaEventRecord(c->ev_start, s));
+  for (int q = 0; q < 3; ++q) HZ_CK(c, cudaStreamWaitEvent(c->ps[q], c->ev_start, 0));
+  for (int w = 0; w < nw; ++w) {
+    const int k = w % PIPE_SLOTS, i = ws[w], m = ws[w + 1] - ws[w];
+    const LaunchPlan& lp = lps[w];
+    uint8_t* base = c->arena.base + slot_off[k];
+    HzJobs jobs;
+    fill_jobs(c, lp, fr + i, m, jobs, tsrc, base);
+    if (chain)
+      for (int f = 0; f < m; ++f) jobs.j[f].state = chain;
+    // stage 1: the slot is free once the reconstruction of wave w - 3 ended
+    if (w >= PIPE_SLOTS) HZ_CK(c, cudaStreamWaitEvent(sa, c->ev_free[k], 0));
+    HZ_CK(c, cudaMemsetAsync(base, 0, lp.zero_bytes, sa));
+    HZ_CK(c, copy_unaligned(lp, fr + i, m, base, sa));
+    HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(max_tiles(jobs), m), sa, jobs));
+    HZ_CK(c, cudaEventRecord(c->ev_dark[k], sa));
+    // stage 2: selection; its last block runs the airlight chain
+    HZ_CK(c, cudaStreamWaitEvent(sb, c->ev_dark[k], 0));
+    {
+      LaunchScope ls(c, HZ_K_SELECT, sb);
+      k_p2<<<dim3(max_tiles(jobs), m), 256, 0, sb>>>(jobs, kp);
+    }
+    HZ_CK(c, cudaGetLastError());
+    HZ_CK(c, cudaEventRecord(c->ev_sel[k], sb));
+    // stage 3: reconstruction, then the wave's records
+    HZ_CK(c, cudaStreamWaitEvent(sc, c->ev_sel[k], 0));
+    HZ_TRY(run_recon(c, jobs, bal, sc));
+    if (recs) HZ_CK(c, cudaMemcpyAsync(recs + i, base, sizeof(HzFrameRec) * size_t(m), cudaMemcpyDeviceToHost, sc));
+    HZ_CK(c, cudaEventRecord(c->ev_free[k], sc));
+  }
+  // ps[2] ends last: every earlier stage of every wave precedes it
+  HZ_CK(c, cudaEventRecord(c->ev_end, sc));
+  HZ_CK(c, cudaStreamWaitEvent(s, c->ev_end, 0));
+  if (infos) {
+    HZ_CK(c, cudaStreamSynchronize(s));
+    for (int w = 0; w < nw; ++w) recs_to_infos(recs + ws[w], lps[w], ws[w + 1] - ws[w], infos + ws[w], bal);
+  }
   return HZ_OK;
+}
+
+// Video frames on device memory: one wave runs on the caller's stream,
+// several go through the pipeline.
+static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
+                              HzStreamState* chain, HzFrameRec* rec_sink = nullptr) {
+  std::vector<int> ws;
+  split_waves(c, fr, n, ws);
+  if (ws.size() > 2) return video_pipelined(c, fr, ws, s, infos, chain, rec_sink);
+  const bool bal = c->prm.color_balance != 0;
+  const int tsrc = (c->prm.t_mode == HZ_T_FAST) ? TS_FAST : TS_P;
+  LaunchPlan lp;
+  wave_plan(c, fr, 0, n, bal, lp);
+  HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  HZ_CK(c, copy_unaligned(lp, fr, n, c->arena.base, s));
+  HzJobs jobs;
+  fill_jobs(c, lp, fr, n, jobs, tsrc);
+  if (chain)
+    for (int k = 0; k < n; ++k) jobs.j[k].state = chain;
+  HZ_TRY(run_video_jobs(c, lp, jobs, bal, s));
+  if (rec_sink)
+    HZ_CK(c, cudaMemcpyAsync(rec_sink, c->arena.base, sizeof(HzFrameRec) * size_t(n), cudaMemcpyDeviceToHost, s));
+  return read_infos(c, lp, n, s, infos, bal);
 }
 
 extern "C" hz_status hz_dehaze_frame(hz_ctx* c, int32_t stream_id, const uint8_t* in, int32_t W, int32_t H,
@@ -851,6 +969,19 @@ extern "C" hz_status hz_guided_filter(hz_ctx* c, const uint8_t* in, int32_t W, i
 
 // ------------------------------------------------------------ profiling --
 
+extern "C" hz_status hz_set_wave_bytes(hz_ctx* c, size_t bytes) {
+  if (!c) return HZ_EINVAL;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->wave_bytes = bytes ? bytes : hz::DEFAULT_WAVE_BYTES;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return HZ_EINVAL;
+  *bytes = c->wave_bytes;
+  return HZ_OK;
+}
+
 extern "C" hz_status hz_set_profiling(hz_ctx* c, int on) {
   if (!c) return HZ_EINVAL;
   std::lock_guard<std::mutex> lk(c->pmu);
@@ -1002,6 +1133,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   j.P = base + f.off_P;
   j.P_pitch = f.P_pitch;
   j.tilemax = base + f.off_tilemax;
+  j.rowmax = base + f.off_rowmax;
   j.rowcnt = reinterpret_cast<unsigned*>(base + f.off_rowcnt);
   j.rowsum = reinterpret_cast<unsigned*>(base + f.off_rowsum);
   j.rec = reinterpret_cast<HzFrameRec*>(base + f.off_rec);
@@ -1026,7 +1158,6 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
       default: break;
     }
     k_p2<<<g1, 256, 0, s>>>(jobs, kp);
-    k_fin<<<1, FIN_THREADS, 0, s>>>(jobs, kp);
     if (bal) {
       k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
       k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);

@@ -32,8 +32,10 @@ __device__ __forceinline__ void slide_min(uint32_t (&v)[L]) {
   }
 }
 
-// Block-wide inclusive scan of one unsigned per thread (blockDim 256).
-__device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* sh /*>= 8*/, unsigned* total) {
+// Block-wide inclusive scan of one unsigned per thread, for blocks of NW
+// full warps (sh holds NW values).
+template <int NW = 8>
+__device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* sh, unsigned* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -44,7 +46,7 @@ __device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* sh /*>
   __syncthreads();
   unsigned add = 0, tot = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
+  for (int w = 0; w < NW; ++w) {
     unsigned s = sh[w];
     if (w < wid) add += s;
     tot += s;
@@ -54,8 +56,10 @@ __device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* sh /*>
   return v + add;
 }
 
-template <typename T>
-__device__ __forceinline__ T block_sum256(T v, T* sh /*>= 8*/) {
+// Block-wide sum over NW full warps, fixed order (valid in thread 0; sh
+// holds NW values).
+template <int NW = 8, typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) sh[wid] = v;
@@ -63,10 +67,10 @@ __device__ __forceinline__ T block_sum256(T v, T* sh /*>= 8*/) {
   T s = T(0);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += sh[w];
+    for (int w = 0; w < NW; ++w) s += sh[w];
   }
   __syncthreads();
-  return s;  // valid in thread 0
+  return s;
 }
 
 // ------------------------------------------------------------------------
@@ -113,7 +117,8 @@ struct P1S {
   static constexpr int NCK = ((E0B + 3 * (P1_HSEG + 2 * R) + 3) >> 4) + 1;  // 16-byte chunks per item
   static constexpr int NIN = P1_HSEG + 2 * R;                   // staged pixels per horizontal item
   static constexpr int OFF_HIST = ((NCH * CH * SLOT) + 15) / 16 * 16;
-  static constexpr int OFF_MBAR = OFF_HIST + (NT / 32) * 256 * 4;
+  static constexpr int NHIST = 4;                               // histogram copies (warps share)
+  static constexpr int OFF_MBAR = OFF_HIST + NHIST * 256 * 4;
   static constexpr int SMEM = OFF_MBAR + NCH * 8 + 16;
 };
 
@@ -331,7 +336,7 @@ __device__ __forceinline__ void p1_hitem(const uint4* vq, int sp0, int W, int nv
 }
 
 template <int R>
-__device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned char* smem) {
+__device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned char* smem) {
   using G = P1S<R>;
   constexpr int P = G::P;
   const int tid = threadIdx.x;
@@ -349,7 +354,7 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
   __shared__ unsigned red[32];
   __shared__ int s_last, s_fail;
 
-  for (int i = tid; i < (G::NT / 32) * 256; i += G::NT) whist[i] = 0u;
+  for (int i = tid; i < G::NHIST * 256; i += G::NT) whist[i] = 0u;
   if (tid == 0) {
     s_fail = 0;
     for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
@@ -384,12 +389,15 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
   if (s_fail) {
     for (int c = 0; c < G::NCH; ++c) (void)mbar_wait_bounded(mbar + c, 0u);
     if (tid == 0) jb.rec->status = HZ_STATUS_DEVICE_TIMEOUT;
-    return;
+    return false;
   }
 
   // ---- phase 2: horizontal minima, (row, 64-pixel segment) per thread ----
+  __shared__ unsigned s_rowmax[64];
+  for (int k = tid; k < 64; k += G::NT) s_rowmax[k] = 0u;
+  __syncthreads();
   unsigned tmax = 0;
-  unsigned* hw = whist + (tid >> 5) * 256;
+  unsigned* hw = whist + ((tid >> 5) % G::NHIST) * 256;
   for (int it = tid; it < bh * P1_NSEG; it += G::NT) {
     const int seg = it / bh, k = it - seg * bh;
     const int xo = x0 + seg * P1_HSEG;  // first output pixel
@@ -399,8 +407,11 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
     const bool edge = (sp0 < 0) || (sp0 + G::NIN > W);
     uint4* Pp = reinterpret_cast<uint4*>(jb.P + (long long)(y0 + k) * jb.P_pitch + 3LL * xo);
     uint8_t* Dp = jb.Dout ? jb.Dout + (long long)(y0 + k) * jb.D_pitch + xo : nullptr;
-    if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw, tmax);
-    else p1_hitem<R, false>(vq, sp0, W, P1_HSEG, Pp, nullptr, hw, tmax);
+    unsigned imax = 0;
+    if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw, imax);
+    else p1_hitem<R, false>(vq, sp0, W, P1_HSEG, Pp, nullptr, hw, imax);
+    tmax = max(tmax, imax);
+    atomicMax(&s_rowmax[k], imax);
   }
   // region maximum and histogram
 #pragma unroll
@@ -410,7 +421,7 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
   for (int bin = tid; bin < 256; bin += G::NT) {
     unsigned sum = 0;
 #pragma unroll
-    for (int w = 0; w < G::NT / 32; ++w) sum += whist[w * 256 + bin];
+    for (int w = 0; w < G::NHIST; ++w) sum += whist[w * 256 + bin];
     if (sum) atomicAdd(&jb.rec->hist[bin], sum);
   }
   if (tid == 0) {
@@ -418,6 +429,8 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
     for (int w = 0; w < G::NT / 32; ++w) m = max(m, red[w]);
     jb.tilemax[item] = uint8_t(m);
   }
+  if (jb.rowmax)
+    for (int k = tid; k < bh; k += G::NT) jb.rowmax[(long long)(y0 + k) * jb.tiles_x + strip] = uint8_t(s_rowmax[k]);
   __threadfence();
   __syncthreads();
   if (tid == 0) {
@@ -425,7 +438,9 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
     s_last = (atomicAdd(&jb.rec->done_p1, 1u) == nitems - 1u);
   }
   __syncthreads();
-  if (!s_last) return;
+  if (tid == 0)
+    for (int c = 0; c < G::NCH; ++c) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar + c)));
+  if (!s_last) return false;
   __threadfence();
   // suffix counts S(v) = #(D >= v); T = max{v : S(v) >= K}, scanned by the
   // first 256 threads
@@ -450,6 +465,7 @@ __device__ __forceinline__ void p1_region(const HzJob& jb, int item, unsigned ch
       jb.rec->m_ties = (long long)(K - excl);
     }
   }
+  return true;
 }
 
 template <int R>
@@ -464,18 +480,18 @@ __global__ void __launch_bounds__(P1S<R>::NT) k_p1(const __grid_constant__ HzJob
 // ------------------------------------------------------------------------
 // p2: candidate tiles of the selection, and the raster-order cut.
 __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
-  __shared__ unsigned sh[8];
-  __shared__ unsigned long long shl[8];
-  __shared__ int s_found;
-  __shared__ int s_row;
+  __shared__ unsigned sh[32];
+  __shared__ unsigned long long shl[32];
+  __shared__ int s_found, s_row, s_cut;
   __shared__ unsigned s_need;
-  __shared__ int s_cut;
   const int tid = threadIdx.x;
+  constexpr int NTH = 256;  // k_p2 block
   HzFrameRec* rec = jb.rec;
   const int H = jb.H, W = jb.W;
-  const unsigned m = (unsigned)rec->m_ties;
-  const int T = rec->T;
-  // rows before the cut row, by an ordered scan of per-row tie counts
+  const unsigned m = (unsigned)__ldcg(&rec->m_ties);
+  const int T = __ldcg(&rec->T);
+  // rows before the cut row: ordered scan of the per-row tie counts, one
+  // row per thread and pass, stopping at the pass that reaches m
   unsigned base = 0;
   unsigned long long sr = 0, sg = 0, sb = 0;
   if (tid == 0) {
@@ -484,18 +500,17 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
     s_need = 0;
   }
   __syncthreads();
-  for (int y0 = 0; y0 < H; y0 += 256) {
+  for (int y0 = 0; y0 < H; y0 += NTH) {
     const int y = y0 + tid;
     const unsigned c = (y < H) ? __ldcg(&jb.rowcnt[y]) : 0u;
     unsigned tot;
     const unsigned incl = block_scan_incl(c, sh, &tot);
-    const bool before = (y < H) && (base + incl < m);
-    if ((y < H) && (base + incl >= m) && (base + incl - c < m)) {
+    if (y < H && base + incl >= m && base + incl - c < m) {
       s_row = y;
       s_need = m - (base + incl - c);
       s_found = 1;
     }
-    if (before) {
+    if (y < H && base + incl < m) {
       sr += __ldcg(&jb.rowsum[3 * y + 0]);
       sg += __ldcg(&jb.rowsum[3 * y + 1]);
       sb += __ldcg(&jb.rowsum[3 * y + 2]);
@@ -504,27 +519,28 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
     __syncthreads();
     if (s_found) break;
   }
-  unsigned long long rs = block_sum256(sr, shl);
-  unsigned long long gs = block_sum256(sg, shl);
-  unsigned long long bs = block_sum256(sb, shl);
+  const unsigned long long rs = block_sum(sr, shl);
+  const unsigned long long gs = block_sum(sg, shl);
+  const unsigned long long bs = block_sum(sb, shl);
   if (!s_found) {  // tie counts inconsistent with the histogram: report, touch nothing
     if (tid == 0) rec->status = HZ_STATUS_SELECT_FAILED;
     return;
   }
   const int ystar = s_row;
   const unsigned need = s_need;
-  // the cut row: ties in column order
+  // the cut row: ties in column order, one pixel per thread and pass
   const uint8_t* Prow = jb.P + (long long)ystar * jb.P_pitch;
   const uint8_t* Irow = jb.in + (long long)ystar * jb.in_pitch;
   unsigned long long cr = 0, cg = 0, cb = 0;
   unsigned rank0 = 0;
   if (tid == 0) s_cut = -1;
   __syncthreads();
-  for (int xb = 0; xb < W; xb += 256) {
+  for (int xb = 0; xb < W; xb += NTH) {
     const int x = xb + tid;
     unsigned tie = 0;
     if (x < W) {
-      const unsigned d = min(min((unsigned)Prow[3 * x], (unsigned)Prow[3 * x + 1]), (unsigned)Prow[3 * x + 2]);
+      const unsigned d = min(min((unsigned)__ldcg(Prow + 3 * x), (unsigned)__ldcg(Prow + 3 * x + 1)),
+                             (unsigned)__ldcg(Prow + 3 * x + 2));
       tie = (d == (unsigned)T) ? 1u : 0u;
     }
     unsigned tot;
@@ -539,13 +555,13 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
     __syncthreads();
     if (rank0 >= need) break;
   }
-  unsigned long long rr = block_sum256(cr, shl);
-  unsigned long long rg = block_sum256(cg, shl);
-  unsigned long long rb = block_sum256(cb, shl);
+  const unsigned long long rr = block_sum(cr, shl);
+  const unsigned long long rg = block_sum(cg, shl);
+  const unsigned long long rb = block_sum(cb, shl);
   if (tid == 0) {
-    const unsigned long long S0 = rec->S_above[0] + rs + rr;
-    const unsigned long long S1 = rec->S_above[1] + gs + rg;
-    const unsigned long long S2 = rec->S_above[2] + bs + rb;
+    const unsigned long long S0 = __ldcg(&rec->S_above[0]) + rs + rr;
+    const unsigned long long S1 = __ldcg(&rec->S_above[1]) + gs + rg;
+    const unsigned long long S2 = __ldcg(&rec->S_above[2]) + bs + rb;
     rec->S[0] = S0; rec->S[1] = S1; rec->S[2] = S2;
     rec->cut_index = (long long)ystar * W + s_cut;
     const double den = 255.0 * double(jb.K);
@@ -556,99 +572,87 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
-  const HzJob& jb = jobs.j[blockIdx.y];
-  const int item = blockIdx.x;
-  const int nitems = jb.tiles_x * jb.tiles_y;
-  if (item >= nitems) return;
-  __shared__ unsigned long long shl[8];
-  __shared__ int s_last;
+// Candidate region of the selection: pixels with D > T add to the frame's
+// r/g/b sums, ties (D == T) to per-row counts and sums; rows whose maximum
+// stays below T are skipped.
+__device__ void p2_scan_region(const HzJob& jb, int item, int T) {
+  __shared__ unsigned long long shl[32];
+  constexpr int nw = 8;  // k_p2 block
   const int tid = threadIdx.x;
   HzFrameRec* rec = jb.rec;
-  const int T = rec->T;
-  if ((int)jb.tilemax[item] >= T) {
-    const int strip = item % jb.tiles_x, band = item / jb.tiles_x;
-    const int x0 = strip * P1_SW, y0 = band * jb.band_h;
-    const int lane = tid & 31, wid = tid >> 5;
-    unsigned ar = 0, ag = 0, ab = 0;
-    for (int i = wid; i < jb.band_h; i += 8) {
-      const int y = y0 + i;
-      if (y >= jb.H) break;
-      unsigned tr = 0, tg = 0, tb = 0, tc = 0;
-      for (int xq = 0; xq < P1_SW; xq += 128) {
-        const int x = x0 + xq + 4 * lane;
-        if (xq + 4 * lane >= P1_SW || x >= jb.W) continue;
-        const uint32_t* Pp = reinterpret_cast<const uint32_t*>(jb.P + (long long)y * jb.P_pitch + 3LL * x);
-        const uint32_t bytes[3] = {__ldcg(Pp), __ldcg(Pp + 1), __ldcg(Pp + 2)};
-        const int nv = min(4, jb.W - x);
-        const uint8_t* Ip = jb.in + (long long)y * jb.in_pitch + 3LL * x;
-        for (int k = 0; k < nv; ++k) {
-          unsigned v[3];
+  const int strip = item % jb.tiles_x, band = item / jb.tiles_x;
+  const int x0 = strip * P1_SW, y0 = band * jb.band_h;
+  const int lane = tid & 31, wid = tid >> 5;
+  unsigned ar = 0, ag = 0, ab = 0;
+  for (int i = wid; i < jb.band_h; i += nw) {
+    const int y = y0 + i;
+    if (y >= jb.H) break;
+    if (jb.rowmax && (int)__ldcg(jb.rowmax + (long long)y * jb.tiles_x + strip) < T) continue;
+    unsigned tr = 0, tg = 0, tb = 0, tc = 0;
+    for (int xq = 0; xq < P1_SW; xq += 128) {
+      const int x = x0 + xq + 4 * lane;
+      if (xq + 4 * lane >= P1_SW || x >= jb.W) continue;
+      const uint32_t* Pp = reinterpret_cast<const uint32_t*>(jb.P + (long long)y * jb.P_pitch + 3LL * x);
+      const uint32_t bytes[3] = {__ldcg(Pp), __ldcg(Pp + 1), __ldcg(Pp + 2)};
+      const int nv = min(4, jb.W - x);
+      const uint8_t* Ip = jb.in + (long long)y * jb.in_pitch + 3LL * x;
+      for (int k = 0; k < nv; ++k) {
+        unsigned v[3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int bi = 3 * k + c;
-            v[c] = (bytes[bi >> 2] >> (8 * (bi & 3))) & 0xff;
-          }
-          const int d = (int)min(min(v[0], v[1]), v[2]);
-          if (d >= T) {
-            const unsigned r = Ip[3 * k], g = Ip[3 * k + 1], b = Ip[3 * k + 2];
-            if (d > T) {
-              ar += r; ag += g; ab += b;
-            } else {
-              tr += r; tg += g; tb += b; ++tc;
-            }
-          }
+        for (int c = 0; c < 3; ++c) {
+          const int bi = 3 * k + c;
+          v[c] = (bytes[bi >> 2] >> (8 * (bi & 3))) & 0xff;
         }
-      }
-      tc = warp_sum(tc);
-      if (tc) {
-        tr = warp_sum(tr);
-        tg = warp_sum(tg);
-        tb = warp_sum(tb);
-        if (lane == 0) {
-          atomicAdd(&jb.rowcnt[y], tc);
-          atomicAdd(&jb.rowsum[3 * y + 0], tr);
-          atomicAdd(&jb.rowsum[3 * y + 1], tg);
-          atomicAdd(&jb.rowsum[3 * y + 2], tb);
+        const int d = (int)min(min(v[0], v[1]), v[2]);
+        if (d >= T) {
+          const unsigned r = Ip[3 * k], g = Ip[3 * k + 1], b = Ip[3 * k + 2];
+          if (d > T) {
+            ar += r; ag += g; ab += b;
+          } else {
+            tr += r; tg += g; tb += b; ++tc;
+          }
         }
       }
     }
-    unsigned long long s0 = block_sum256((unsigned long long)ar, shl);
-    unsigned long long s1 = block_sum256((unsigned long long)ag, shl);
-    unsigned long long s2 = block_sum256((unsigned long long)ab, shl);
-    if (tid == 0 && (s0 | s1 | s2)) {
-      atomicAdd(&rec->S_above[0], s0);
-      atomicAdd(&rec->S_above[1], s1);
-      atomicAdd(&rec->S_above[2], s2);
+    tc = warp_sum(tc);
+    if (tc) {
+      tr = warp_sum(tr);
+      tg = warp_sum(tg);
+      tb = warp_sum(tb);
+      if (lane == 0) {
+        atomicAdd(&jb.rowcnt[y], tc);
+        atomicAdd(&jb.rowsum[3 * y + 0], tr);
+        atomicAdd(&jb.rowsum[3 * y + 1], tg);
+        atomicAdd(&jb.rowsum[3 * y + 2], tb);
+      }
     }
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  p2_finalize(jb, kp);
+  unsigned long long s0 = block_sum((unsigned long long)ar, shl);
+  unsigned long long s1 = block_sum((unsigned long long)ag, shl);
+  unsigned long long s2 = block_sum((unsigned long long)ab, shl);
+  if (tid == 0 && (s0 | s1 | s2)) {
+    atomicAdd(&rec->S_above[0], s0);
+    atomicAdd(&rec->S_above[1], s1);
+    atomicAdd(&rec->S_above[2], s2);
+  }
 }
 
-// ------------------------------------------------------------------------
-// Airlight finish, frames in launch order: override, or smoothing
-// A_f = lam A_{f-1} + (1 - lam) A_hat_f through each frame's stream state.
-// Loads and stores are spread over the block; the chain itself runs in one
-// thread on shared memory.
-constexpr int FIN_THREADS = 64;
-__global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+// Airlight of the launch's frames in order: override, or smoothing
+// A_f = lam A_{f-1} + (1 - lam) A_hat_f through each frame's stream state,
+// then the 1/A factors. Loads and stores are spread over the block; the chain
+// runs in one thread on shared memory.
+__device__ void fin_frames(const HzJobs& jobs, const HzKParams& kp) {
   __shared__ double sAh[MAXJ][3];
   __shared__ double sA[MAXJ][3];
   __shared__ HzStreamState* sptr[MAXJ];
   __shared__ double sst[MAXJ][3];
   __shared__ long long sfr[MAXJ];
   const int n = jobs.n, tid = threadIdx.x;
-  for (int f = tid; f < n; f += FIN_THREADS) {
+  for (int f = tid; f < n; f += blockDim.x) {
     const HzFrameRec* rec = jobs.j[f].rec;
-    sAh[f][0] = rec->A_hat[0];
-    sAh[f][1] = rec->A_hat[1];
-    sAh[f][2] = rec->A_hat[2];
+    sAh[f][0] = __ldcg(&rec->A_hat[0]);
+    sAh[f][1] = __ldcg(&rec->A_hat[1]);
+    sAh[f][2] = __ldcg(&rec->A_hat[2]);
   }
   __syncthreads();
   if (tid == 0) {
@@ -664,8 +668,8 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJ
         while (k < nst && sptr[k] != jb.state) ++k;
         if (k == nst) {
           sptr[k] = jb.state;
-          for (int c = 0; c < 3; ++c) sst[k][c] = jb.state->A[c];
-          sfr[k] = jb.state->frames;
+          for (int c = 0; c < 3; ++c) sst[k][c] = __ldcg(&jb.state->A[c]);
+          sfr[k] = __ldcg(&jb.state->frames);
           ++nst;
         }
         if (kp.ema > 0.f && sfr[k] > 0) {
@@ -686,7 +690,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJ
     }
   }
   __syncthreads();
-  for (int f = tid; f < n; f += FIN_THREADS) {
+  for (int f = tid; f < n; f += blockDim.x) {
     HzFrameRec* rec = jobs.j[f].rec;
     double amax = 0.0;
     for (int c = 0; c < 3; ++c) {
@@ -699,6 +703,75 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJ
     }
     rec->inv_fast = float(1.0 / (255.0 * amax));
   }
+}
+
+// Selection of every frame of the launch; the last block of a frame cuts
+// its ties and forms A_hat, the last block of the launch runs the airlight
+// chain of all frames (launch counter in the first frame's record).
+__global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+  const HzJob& jb = jobs.j[blockIdx.y];
+  const int item = blockIdx.x;
+  const int nitems = jb.tiles_x * jb.tiles_y;
+  if (item >= nitems) return;
+  __shared__ int s_last, s_all;
+  const int tid = threadIdx.x;
+  HzFrameRec* rec = jb.rec;
+  const int T = rec->T;
+  if ((int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    p2_finalize(jb, kp);
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned total = 0;
+    for (int f = 0; f < jobs.n; ++f) total += unsigned(jobs.j[f].tiles_x * jobs.j[f].tiles_y);
+    s_all = (atomicAdd(&jobs.j[0].rec->launch_done, 1u) == total - 1u);
+  }
+  __syncthreads();
+  if (!s_all) return;
+  __threadfence();
+  fin_frames(jobs, kp);
+}
+
+// The airlight chain as its own launch (stage calls that skip selection).
+constexpr int FIN_THREADS = 64;
+__global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+  fin_frames(jobs, kp);
+}
+
+// Airlight of one frame (thread 0): override, or smoothing through the
+// frame's stream state, and the 1/A factors of the reconstruction.
+__device__ void fin_one(const HzJob& jb, const HzKParams& kp) {
+  HzFrameRec* rec = jb.rec;
+  double A[3];
+  const double Ah[3] = {__ldcg(&rec->A_hat[0]), __ldcg(&rec->A_hat[1]), __ldcg(&rec->A_hat[2])};
+  if (jb.use_override) {
+    for (int c = 0; c < 3; ++c) A[c] = double(kp.ov[c]);
+  } else if (jb.state) {
+    const long long nf = __ldcg(&jb.state->frames);
+    const double lam = double(kp.ema);
+    for (int c = 0; c < 3; ++c)
+      A[c] = (kp.ema > 0.f && nf > 0) ? lam * __ldcg(&jb.state->A[c]) + (1.0 - lam) * Ah[c] : Ah[c];
+    for (int c = 0; c < 3; ++c) jb.state->A[c] = A[c];
+    jb.state->frames = nf + 1;
+  } else {
+    for (int c = 0; c < 3; ++c) A[c] = Ah[c];
+  }
+  double amax = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    rec->A_used[c] = A[c];
+    rec->A[c] = float(A[c]);
+    const double af = fmax(double(float(A[c])), double(A_FLOOR));
+    rec->inv[c] = float(1.0 / (255.0 * af));
+    amax = fmax(amax, af);
+  }
+  rec->inv_fast = float(1.0 / (255.0 * amax));
 }
 
 // ------------------------------------------------------------------------
@@ -778,15 +851,14 @@ __device__ __forceinline__ float jg_of(float vbits, int c, float rt, const P3Con
   return Jg;
 }
 
+// One reconstruction unit (P3_THREADS groups of 16 pixels) of a frame;
+// threads past P3_THREADS do nothing (except in the M_BAL_SUMS reductions).
 template <int MODE>
-__global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
-  const HzJob& jb = jobs.j[blockIdx.y];
+__device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, int unit) {
   const int W = jb.W, H = jb.H;
   const int gpr = (W + P3_GPX - 1) / P3_GPX;  // pixel groups per row
   const long long ngroups = (long long)gpr * H;
   const int nunits = int((ngroups + P3_THREADS - 1) / P3_THREADS);
-  const int unit = blockIdx.x;
-  if (unit >= nunits) return;
   const int tid = threadIdx.x;
   const long long g = (long long)unit * P3_THREADS + tid;
   const HzFrameRec* rec = jb.rec;
@@ -801,7 +873,7 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
   K.inv_fast = rec->inv_fast;
   K.ninv_fast = -TWO23 * K.inv_fast;
   float js0 = 0.f, js1 = 0.f, js2 = 0.f;
-  if (g < ngroups) {
+  if (tid < P3_THREADS && g < ngroups) {
     const int y = int(g / gpr);
     const int x = int(g - (long long)y * gpr) * P3_GPX;
     const int nv = min(P3_GPX, W - x);
@@ -884,12 +956,12 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
     }
   }
   if constexpr (MODE == M_BAL_SUMS) {
-    __shared__ double shd[8];
+    __shared__ double shd[32];
     __shared__ int s_last;
     HzFrameRec* wrec = jb.rec;
-    const double d0 = block_sum256((double)js0, shd);
-    const double d1 = block_sum256((double)js1, shd);
-    const double d2 = block_sum256((double)js2, shd);
+    const double d0 = block_sum((double)js0, shd);
+    const double d1 = block_sum((double)js1, shd);
+    const double d2 = block_sum((double)js2, shd);
     if (tid == 0) {
       jb.bal_part[3 * unit + 0] = d0;
       jb.bal_part[3 * unit + 1] = d1;
@@ -908,9 +980,9 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
       a1 += __ldcg(&jb.bal_part[3 * u + 1]);
       a2 += __ldcg(&jb.bal_part[3 * u + 2]);
     }
-    const double t0 = block_sum256(a0, shd);
-    const double t1 = block_sum256(a1, shd);
-    const double t2 = block_sum256(a2, shd);
+    const double t0 = block_sum(a0, shd);
+    const double t1 = block_sum(a1, shd);
+    const double t2 = block_sum(a2, shd);
     if (tid == 0) {
       const double N = double(jb.W) * double(jb.H);
       const double mu[3] = {t0 / N, t1 / N, t2 / N};
@@ -921,6 +993,14 @@ __global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJob
       }
     }
   }
+}
+
+
+template <int MODE>
+__global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+  const HzJob& jb = jobs.j[blockIdx.y];
+  if ((int)blockIdx.x >= p3_units(jb.W, jb.H)) return;
+  p3_unit<MODE>(jb, kp, blockIdx.x);
 }
 
 }  // namespace hz

@@ -27,6 +27,8 @@ struct Arena {
   size_t cap = 0;
 };
 
+constexpr size_t DEFAULT_WAVE_BYTES = size_t(20) << 20;  // input bytes per wave of frames
+
 }  // namespace hz
 
 struct hz_ctx {
@@ -42,6 +44,15 @@ struct hz_ctx {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   bool have_done = false;
+  // wave pipeline: dark channel, selection and reconstruction streams, and
+  // per-slot events (a wave owns slot w % PIPE_SLOTS of the arena)
+  cudaStream_t ps[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_dark[3] = {nullptr, nullptr, nullptr}, ev_sel[3] = {nullptr, nullptr, nullptr},
+              ev_free[3] = {nullptr, nullptr, nullptr};
+  hz::HzFrameRec* rec_pinned = nullptr;  // pinned, rec_pinned_cap records
+  size_t rec_pinned_cap = 0;
+  size_t wave_bytes = hz::DEFAULT_WAVE_BYTES;  // input bytes per wave
   // stream table
   std::mutex smu;
   int stream_open[hz::MAX_STREAMS] = {0};
@@ -99,7 +110,7 @@ struct FramePlan {
   long long K;
   long long P_pitch;
   size_t off_rec, off_rowcnt, off_rowsum;  // in the zeroed region
-  size_t off_P, off_tilemax, off_bal;      // in the rest
+  size_t off_P, off_tilemax, off_rowmax, off_bal;  // in the rest
   size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
   long long plane_pitch32, plane_pitch16;
   size_t off_copy;                          // aligned copy of an unaligned input (0 if none)
@@ -157,6 +168,8 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     o = align_up(o + size_t(f.P_pitch) * f.H, 1024);
     f.off_tilemax = o;
     o = align_up(o + size_t(f.tiles_x) * f.tiles_y, 256);
+    f.off_rowmax = o;
+    o = align_up(o + size_t(f.tiles_x) * f.H, 256);
     f.off_bal = 0;
     if (balance) {
       f.off_bal = o;
@@ -233,7 +246,8 @@ hz_status order_after_previous(hz_ctx* c, cudaStream_t s);
 hz_status mark_done(hz_ctx* c, cudaStream_t s);
 
 // Build the jobs of one launch from a plan (device pointers inside arena).
-void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video);
+void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video,
+               uint8_t* base = nullptr);
 
 // Video-mode pipeline for up to MAXJ frames already described in `jobs`.
 hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s);

@@ -266,3 +266,39 @@ def test_full_size_1080p_frame():
     assert list(infos[0].S) == [int(v) for v in ref.S]
     mx, exact = u8_diff(o, ref.out)
     assert mx <= 1 and exact > 0.995
+
+
+@pytest.mark.parametrize("kw", [dict(airlight_ema=0.9), dict(airlight_ema=0.9, color_balance=1),
+                                dict(t_mode=1, omega=0.5, t0=0.05)])
+def test_wave_pipeline_matches_one_wave(kw):
+    """Several waves run through the three-stream pipeline (one frame, or
+    four frames, per wave, reusing the three scratch slots); the results
+    equal one wave on the call's stream and the oracle's sequence."""
+    W, H, F = 333, 251, 11
+    frames = hazegen.make_sequence(W, H, F, seed=9, period=F)
+    specs = [(854, 480, 3), (1280, 720, 4), (640, 480, 5), (97, 61, 6), (1920, 1080, 7)]
+    mixed = [hazegen.make_frame(w, h, seed=sd) for (w, h, sd) in specs]
+    res = {}
+    with context(**kw) as (m, ctx):
+        assert m.hz_get_wave_bytes(ctx) == 20 << 20
+        for wb in (1, 4 * 3 * W * H, 0):
+            m.hz_set_wave_bytes(ctx, wb)
+            inp = torch.from_numpy(frames).cuda()
+            out = torch.empty_like(inp)
+            infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
+            ins = [to_dev(I, 3) for I in mixed]  # unaligned: copied into the wave's slot
+            outs = [empty_dev(w, h, 1)[0] for (w, h, _) in specs]
+            binfos = m.hz_dehaze_batch(ctx, ins, outs, want_info=True)
+            res[wb] = (out.cpu().numpy(), [(list(i.A), i.T, i.cut_index) for i in infos],
+                       [o.cpu().numpy() for o in outs], [(list(i.A), i.T, i.cut_index) for i in binfos])
+        assert m.hz_get_wave_bytes(ctx) == 20 << 20
+    for wb in (1, 4 * 3 * W * H):
+        np.testing.assert_array_equal(res[wb][0], res[0][0])
+        assert res[wb][1] == res[0][1] and res[wb][3] == res[0][3]
+        for a, b in zip(res[wb][2], res[0][2]):
+            np.testing.assert_array_equal(a, b)
+    ref = O.dehaze_sequence(list(frames), oracle_params(**kw))
+    for f in range(F):
+        assert res[1][1][f][1] == ref[f].T and res[1][1][f][2] == ref[f].cut_index
+        mx, exact = u8_diff(res[1][0][f], ref[f].out)
+        assert mx <= 1 and exact > 0.99
