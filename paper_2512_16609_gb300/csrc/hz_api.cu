@@ -410,7 +410,7 @@ extern "C" hz_status hz_create(const hz_params* p, int device, size_t mem_budget
   if (ok)
     ok = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) == cudaSuccess;
-  for (int i = 0; ok && i < 2; ++i)
+  for (int i = 0; ok && i < HOSTIO_BUFS; ++i)
     ok = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
@@ -434,7 +434,7 @@ extern "C" hz_status hz_destroy(hz_ctx* c) {
   if (c->states) cudaFree(c->states);
   if (c->rec_host) cudaFreeHost(c->rec_host);
   if (c->done_ev) cudaEventDestroy(c->done_ev);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < HOSTIO_BUFS; ++i) {
     if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
     if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
     if (c->ev_out[i]) cudaEventDestroy(c->ev_out[i]);
@@ -742,30 +742,37 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
     HZ_TRY(video_device(c, fr.data(), n_frames, s, infos, chain));
     return mark_done(c, s);
   }
-  // host buffers: waves of frames staged through two device buffer pairs;
-  // H2D of wave k+1 (copy_in) and D2H of wave k-1 (copy_out) overlap the
-  // compute of wave k (s).
+  // host buffers: waves of frames staged through HOSTIO_BUFS device buffer
+  // pairs; the H2D copy of wave k+1 (copy_in), the compute of wave k (s) and
+  // the D2H copy of wave k-1 (copy_out) overlap, so both link directions stay
+  // busy. Frames that are contiguous on the host move in one copy per wave.
   const size_t fin = size_t(3) * W * H, fout = fin;
-  int G = (int)std::max<size_t>(1, (size_t(48) << 20) / std::max<size_t>(fin, 1));
+  int G = (int)std::max<size_t>(1, HOSTIO_WAVE_BYTES / std::max<size_t>(fin, 1));
   G = std::min(G, MAXJ);
   G = std::min(G, n_frames);
+  const bool in_contig = in_pitch == size_t(3) * W && in_frame_stride == fin;
+  const bool out_contig = out_pitch == size_t(3) * W && out_frame_stride == fout;
   const size_t half = align_up(size_t(G) * (fin + fout), 4096);
-  HZ_TRY(arena_reserve(c, c->stage, 2 * half, s));
+  HZ_TRY(arena_reserve(c, c->stage, HOSTIO_BUFS * half, s));
   HZ_CK(c, cudaEventRecord(c->ev_comp[0], s));
   HZ_CK(c, cudaStreamWaitEvent(c->copy_in, c->ev_comp[0], 0));
   HZ_CK(c, cudaStreamWaitEvent(c->copy_out, c->ev_comp[0], 0));
   const int nw = (n_frames + G - 1) / G;
-  bool out_pending[2] = {false, false};
+  bool out_pending[HOSTIO_BUFS] = {};
   for (int w = 0; w < nw; ++w) {
-    const int b = w & 1;
+    const int b = w % HOSTIO_BUFS;
     const int f0 = w * G, m = std::min(G, n_frames - f0);
     uint8_t* din = c->stage.base + b * half;
     uint8_t* dout = din + size_t(G) * fin;
     // the buffer pair b is free once its previous D2H finished
     if (out_pending[b]) HZ_CK(c, cudaStreamWaitEvent(c->copy_in, c->ev_out[b], 0));
-    for (int k = 0; k < m; ++k)
-      HZ_CK(c, cudaMemcpy2DAsync(din + size_t(k) * fin, size_t(3) * W, in + size_t(f0 + k) * in_frame_stride,
-                                 in_pitch, size_t(3) * W, H, cudaMemcpyHostToDevice, c->copy_in));
+    if (in_contig) {
+      HZ_CK(c, cudaMemcpyAsync(din, in + size_t(f0) * fin, size_t(m) * fin, cudaMemcpyHostToDevice, c->copy_in));
+    } else {
+      for (int k = 0; k < m; ++k)
+        HZ_CK(c, cudaMemcpy2DAsync(din + size_t(k) * fin, size_t(3) * W, in + size_t(f0 + k) * in_frame_stride,
+                                   in_pitch, size_t(3) * W, H, cudaMemcpyHostToDevice, c->copy_in));
+    }
     HZ_CK(c, cudaEventRecord(c->ev_in[b], c->copy_in));
     HZ_CK(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
     std::vector<hz_frame_desc> fr(m);
@@ -775,14 +782,19 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
     HZ_TRY(video_device(c, fr.data(), m, s, infos ? infos + f0 : nullptr, chain));
     HZ_CK(c, cudaEventRecord(c->ev_comp[b], s));
     HZ_CK(c, cudaStreamWaitEvent(c->copy_out, c->ev_comp[b], 0));
-    for (int k = 0; k < m; ++k)
-      HZ_CK(c, cudaMemcpy2DAsync(out + size_t(f0 + k) * out_frame_stride, out_pitch, dout + size_t(k) * fout,
-                                 size_t(3) * W, size_t(3) * W, H, cudaMemcpyDeviceToHost, c->copy_out));
+    if (out_contig) {
+      HZ_CK(c, cudaMemcpyAsync(out + size_t(f0) * fout, dout, size_t(m) * fout, cudaMemcpyDeviceToHost,
+                               c->copy_out));
+    } else {
+      for (int k = 0; k < m; ++k)
+        HZ_CK(c, cudaMemcpy2DAsync(out + size_t(f0 + k) * out_frame_stride, out_pitch, dout + size_t(k) * fout,
+                                   size_t(3) * W, size_t(3) * W, H, cudaMemcpyDeviceToHost, c->copy_out));
+    }
     HZ_CK(c, cudaEventRecord(c->ev_out[b], c->copy_out));
     out_pending[b] = true;
   }
   // the call's stream completes after the last copy out
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < HOSTIO_BUFS; ++b)
     if (out_pending[b]) HZ_CK(c, cudaStreamWaitEvent(s, c->ev_out[b], 0));
   return mark_done(c, s);
 }

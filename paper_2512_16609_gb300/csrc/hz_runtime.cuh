@@ -28,6 +28,8 @@ struct Arena {
 };
 
 constexpr size_t DEFAULT_WAVE_BYTES = size_t(20) << 20;  // input bytes per wave of frames
+constexpr int HOSTIO_BUFS = 3;                            // staging buffer pairs of host-buffer calls
+constexpr size_t HOSTIO_WAVE_BYTES = size_t(24) << 20;    // input bytes per staged wave
 
 }  // namespace hz
 
@@ -42,7 +44,7 @@ struct hz_ctx {
   hz::HzFrameRec* rec_host = nullptr;   // pinned, MAXJ records
   cudaEvent_t done_ev = nullptr;        // end of the last call's work
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
-  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in[hz::HOSTIO_BUFS] = {}, ev_comp[hz::HOSTIO_BUFS] = {}, ev_out[hz::HOSTIO_BUFS] = {};
   bool have_done = false;
   // wave pipeline: dark channel, selection and reconstruction streams, and
   // per-slot events (a wave owns slot w % PIPE_SLOTS of the arena)

@@ -221,6 +221,29 @@ def test_video_host_io_matches_device_path():
         assert torch.equal(h_out, dev_out.cpu())
 
 
+@pytest.mark.parametrize("pad", [0, 8])
+def test_video_host_io_many_waves(pad):
+    """Host buffers over more staged waves than staging buffers (buffer
+    reuse), with contiguous frames (one copy per wave) and with padded host
+    rows (one 2-D copy per frame)."""
+    W, H, F = 1280, 720, 40
+    frames = hazegen.make_sequence(W, H, 4, seed=6, period=4)
+    frames = np.concatenate([frames] * (F // 4))
+    with context(airlight_ema=0.9) as (m, ctx):
+        dev_in = torch.from_numpy(frames).cuda()
+        dev_out = torch.empty_like(dev_in)
+        ia = m.hz_dehaze_video(ctx, dev_in, dev_out, want_info=True)
+        pitch = 3 * W + pad
+        buf = torch.zeros(F * H * pitch, dtype=torch.uint8).pin_memory()
+        h_in = torch.as_strided(buf, (F, H, W, 3), (H * pitch, pitch, 3, 1))
+        h_in.copy_(torch.from_numpy(frames))
+        h_out = torch.zeros(F, H, W, 3, dtype=torch.uint8).pin_memory()
+        ib = m.hz_dehaze_video(ctx, h_in, h_out, flags=m.HZ_IO_HOST, want_info=True)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out, dev_out.cpu())
+        assert [list(i.A) for i in ia] == [list(i.A) for i in ib]
+
+
 def test_batch_mixed_sizes_matches_single_frames():
     specs = [(854, 480, 1), (1280, 720, 2), (320, 200, 3), (1023, 37, 4), (64, 64, 5)]
     frames = [hazegen.make_frame(W, H, seed=s) for (W, H, s) in specs]
