@@ -41,7 +41,7 @@ ALG_BYTES_PER_PX = 6.0  # read I once, write the output once
 # algorithmic bytes per pixel of each kernel class: what its inputs and
 # outputs must move once (dark: I in, P out; recon: I and P in, out written;
 # fused: the whole path, I in and out written)
-KERNEL_BYTES_PER_PX = {"dark": 6.0, "recon": 9.0, "fused": 6.0, "select": 0.0, "airlight": 0.0}
+KERNEL_BYTES_PER_PX = {"dark": 6.0, "recon": 9.0, "select": 0.0, "airlight": 0.0}
 
 
 def _render_range(args):
@@ -332,13 +332,17 @@ def main():
     px_launch = px_step * args.steps / launches_top
     alg = kbytes.get(top, ALG_BYTES_PER_PX) * px_launch
     achieved = alg / (avg_ms / 1e3) / 1e9
+    # DRAM bytes per pixel of the top kernel from its ncu capture (a smaller
+    # launch of the same kernel), scaled to this launch's pixels
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
-                traffic = json.load(f).get(top)
-        except (OSError, ValueError):
+                ent = json.load(f).get(top)
+            if ent:
+                traffic = ent["bytes_per_px"] * px_launch
+        except (OSError, ValueError, KeyError, TypeError):
             traffic = None
 
     # ---- e2e: same call with pinned host buffers (copies in the region) ---
@@ -472,6 +476,37 @@ def run_served(hzp, dev, frames_by_res, seconds):
             "served": served, "plain_fifo": plain}
 
 
+def host_link_rates(h_in, h_out, d_buf, dev):
+    """Plain copy-engine rates of the host link on the same pinned buffers:
+    a whole-step H2D, a whole-step D2H, and both at once on two streams
+    (the e2e ceiling: every step moves its input in and its output out)."""
+    import torch
+    d_in = torch.empty_like(d_buf)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    nbytes = h_in.numel()
+
+    def timed(h2d, d2h):
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if h2d:
+                with torch.cuda.stream(s1):
+                    d_in.copy_(h_in, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_buf, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            best = dt if best is None else min(best, dt)
+        return best
+
+    t_in, t_out, t_both = timed(True, False), timed(False, True), timed(True, True)
+    del d_in
+    return {"h2d_GBps": nbytes / t_in / 1e9, "d2h_GBps": nbytes / t_out / 1e9,
+            "both_GBps": 2 * nbytes / t_both / 1e9, "ceiling_frames_per_s": F / t_both}
+
+
 def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
     import torch
     h_in = torch.from_numpy(frames_np).pin_memory()
@@ -491,7 +526,9 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
         barrier()
         vals.append(ws * F * e2e_steps / (time.perf_counter() - t0))
     ok = torch.equal(h_out.to(dev), out)
+    link = host_link_rates(h_in, h_out, out, dev)
     return {"value": statistics.median(vals), "unit": "frames/s", "h2d_bytes_per_step": F * W * H * 3,
+            "link": link, "frac_of_link_ceiling": statistics.median(vals) / link["ceiling_frames_per_s"],
             "d2h_bytes_per_step": F * W * H * 3, "matches_device_path": bool(ok),
             "groups_frames_per_s": [round(v, 1) for v in vals], "steps_per_group": e2e_steps,
             "timer": "host wall clock around the calls, synchronised"}
