@@ -114,7 +114,6 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.Dout = nullptr;
     j.D_pitch = 0;
     j.tilemax = A + f.off_tilemax;
-    j.rowmax = A + f.off_rowmax;
     j.rowcnt = reinterpret_cast<unsigned*>(A + f.off_rowcnt);
     j.rowsum = reinterpret_cast<unsigned*>(A + f.off_rowsum);
     j.rec = reinterpret_cast<HzFrameRec*>(A + f.off_rec);
@@ -1145,7 +1144,6 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   j.P = base + f.off_P;
   j.P_pitch = f.P_pitch;
   j.tilemax = base + f.off_tilemax;
-  j.rowmax = base + f.off_rowmax;
   j.rowcnt = reinterpret_cast<unsigned*>(base + f.off_rowcnt);
   j.rowsum = reinterpret_cast<unsigned*>(base + f.off_rowsum);
   j.rec = reinterpret_cast<HzFrameRec*>(base + f.off_rec);

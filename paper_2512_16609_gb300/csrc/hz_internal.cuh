@@ -96,7 +96,6 @@ struct HzJob {
   uint8_t* Dout;                // optional dark channel output
   long long D_pitch;
   uint8_t* tilemax;
-  uint8_t* rowmax;              // [H][tiles_x]: max of D over one row of one strip
   unsigned* rowcnt;             // [H]
   unsigned* rowsum;             // [3H]
   HzFrameRec* rec;

@@ -255,7 +255,7 @@ __device__ __forceinline__ void p1_vblock(unsigned char* smem, int B, int j, uin
 // and may write the dark channel D.
 template <int R, bool EDGE>
 __device__ __forceinline__ void p1_hitem(const uint4* vq, int sp0, int W, int nv, uint4* Pp, uint8_t* Dp,
-                                         unsigned* hw, unsigned& tmax) {
+                                         unsigned* hw) {
   using G = P1S<R>;
   constexpr int P = G::P;
   unsigned cur = 0u, cnt = 0u;
@@ -309,7 +309,6 @@ __device__ __forceinline__ void p1_hitem(const uint4* vq, int sp0, int W, int nv
       const unsigned dv = (vmin2(vmin2(oE, oO), oE >> 16) >> 8) & 0xffu;
       if (!EDGE || u < nv) {
         if (EDGE && Dp) Dp[u] = uint8_t(dv);
-        tmax = max(tmax, dv);
         if (dv == cur) {
           ++cnt;
         } else {
@@ -393,10 +392,6 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
   }
 
   // ---- phase 2: horizontal minima, (row, 64-pixel segment) per thread ----
-  __shared__ unsigned s_rowmax[64];
-  for (int k = tid; k < 64; k += G::NT) s_rowmax[k] = 0u;
-  __syncthreads();
-  unsigned tmax = 0;
   unsigned* hw = whist + ((tid >> 5) % G::NHIST) * 256;
   for (int it = tid; it < bh * P1_NSEG; it += G::NT) {
     const int seg = it / bh, k = it - seg * bh;
@@ -407,33 +402,32 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
     const bool edge = (sp0 < 0) || (sp0 + G::NIN > W);
     uint4* Pp = reinterpret_cast<uint4*>(jb.P + (long long)(y0 + k) * jb.P_pitch + 3LL * xo);
     uint8_t* Dp = jb.Dout ? jb.Dout + (long long)(y0 + k) * jb.D_pitch + xo : nullptr;
-    unsigned imax = 0;
-    if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw, imax);
-    else p1_hitem<R, false>(vq, sp0, W, P1_HSEG, Pp, nullptr, hw, imax);
-    tmax = max(tmax, imax);
-    atomicMax(&s_rowmax[k], imax);
+    if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw);
+    else p1_hitem<R, false>(vq, sp0, W, P1_HSEG, Pp, nullptr, hw);
   }
-  // region maximum and histogram
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-  if ((tid & 31) == 0) red[tid >> 5] = tmax;
   __syncthreads();
+  // histogram into the frame's; the region maximum is its highest bin
+  unsigned top = 0;
   for (int bin = tid; bin < 256; bin += G::NT) {
     unsigned sum = 0;
 #pragma unroll
     for (int w = 0; w < G::NHIST; ++w) sum += whist[w * 256 + bin];
-    if (sum) atomicAdd(&jb.rec->hist[bin], sum);
+    if (sum) {
+      atomicAdd(&jb.rec->hist[bin], sum);
+      top = unsigned(bin) + 1u;
+    }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+  if ((tid & 31) == 0) red[tid >> 5] = top;
+  __syncthreads();
   if (tid == 0) {
     unsigned m = 0;
     for (int w = 0; w < G::NT / 32; ++w) m = max(m, red[w]);
-    jb.tilemax[item] = uint8_t(m);
-  }
-  if (jb.rowmax)
-    for (int k = tid; k < bh; k += G::NT) jb.rowmax[(long long)(y0 + k) * jb.tiles_x + strip] = uint8_t(s_rowmax[k]);
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
+    jb.tilemax[item] = uint8_t(m ? m - 1u : 0u);
+    // one release fence for the block's histogram and maximum (ordered
+    // before it by the barrier), then the region counter
+    __threadfence();
     const unsigned nitems = unsigned(jb.tiles_x * jb.tiles_y);
     s_last = (atomicAdd(&jb.rec->done_p1, 1u) == nitems - 1u);
   }
@@ -573,8 +567,7 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
 }
 
 // Candidate region of the selection: pixels with D > T add to the frame's
-// r/g/b sums, ties (D == T) to per-row counts and sums; rows whose maximum
-// stays below T are skipped.
+// r/g/b sums, ties (D == T) to per-row counts and sums.
 __device__ void p2_scan_region(const HzJob& jb, int item, int T) {
   __shared__ unsigned long long shl[32];
   constexpr int nw = 8;  // k_p2 block
@@ -587,7 +580,6 @@ __device__ void p2_scan_region(const HzJob& jb, int item, int T) {
   for (int i = wid; i < jb.band_h; i += nw) {
     const int y = y0 + i;
     if (y >= jb.H) break;
-    if (jb.rowmax && (int)__ldcg(jb.rowmax + (long long)y * jb.tiles_x + strip) < T) continue;
     unsigned tr = 0, tg = 0, tb = 0, tc = 0;
     for (int xq = 0; xq < P1_SW; xq += 128) {
       const int x = x0 + xq + 4 * lane;
@@ -718,17 +710,20 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   HzFrameRec* rec = jb.rec;
   const int T = rec->T;
   if ((int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
-  __threadfence();
+  // counters: thread 0 releases the block's writes (ordered before it by
+  // the barrier) with one fence, then counts the block
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
+  }
   __syncthreads();
   if (s_last) {
     __threadfence();
-    p2_finalize(jb, kp);
+    p2_finalize(jb, kp);  // its record writes are thread 0's
   }
-  __threadfence();
-  __syncthreads();
   if (tid == 0) {
+    __threadfence();
     unsigned total = 0;
     for (int f = 0; f < jobs.n; ++f) total += unsigned(jobs.j[f].tiles_x * jobs.j[f].tiles_y);
     s_all = (atomicAdd(&jobs.j[0].rec->launch_done, 1u) == total - 1u);
@@ -855,12 +850,13 @@ __device__ __forceinline__ float jg_of(float vbits, int c, float rt, const P3Con
 // threads past P3_THREADS do nothing (except in the M_BAL_SUMS reductions).
 template <int MODE>
 __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, int unit) {
+  // frames hold at most 2^28 pixels, so group indices fit 32 bits
   const int W = jb.W, H = jb.H;
-  const int gpr = (W + P3_GPX - 1) / P3_GPX;  // pixel groups per row
-  const long long ngroups = (long long)gpr * H;
+  const unsigned gpr = unsigned(W + P3_GPX - 1) / P3_GPX;  // pixel groups per row
+  const unsigned ngroups = gpr * unsigned(H);
   const int nunits = int((ngroups + P3_THREADS - 1) / P3_THREADS);
   const int tid = threadIdx.x;
-  const long long g = (long long)unit * P3_THREADS + tid;
+  const unsigned g = unsigned(unit) * P3_THREADS + unsigned(tid);
   const HzFrameRec* rec = jb.rec;
   P3Const K;
 #pragma unroll
@@ -874,8 +870,9 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
   K.ninv_fast = -TWO23 * K.inv_fast;
   float js0 = 0.f, js1 = 0.f, js2 = 0.f;
   if (tid < P3_THREADS && g < ngroups) {
-    const int y = int(g / gpr);
-    const int x = int(g - (long long)y * gpr) * P3_GPX;
+    const unsigned yu = g / gpr;
+    const int y = int(yu);
+    const int x = int(g - yu * gpr) * P3_GPX;
     const int nv = min(P3_GPX, W - x);
     const uint8_t* Ip = jb.in + (long long)y * jb.in_pitch + 3LL * x;
     const uint8_t* Pp = jb.P + (long long)y * jb.P_pitch + 3LL * x;
@@ -966,10 +963,9 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
       jb.bal_part[3 * unit + 0] = d0;
       jb.bal_part[3 * unit + 1] = d1;
       jb.bal_part[3 * unit + 2] = d2;
+      __threadfence();
+      s_last = (atomicAdd(&wrec->done_p3, 1u) == unsigned(nunits) - 1u);
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(&wrec->done_p3, 1u) == unsigned(nunits) - 1u);
     __syncthreads();
     if (!s_last) return;
     __threadfence();

@@ -112,7 +112,7 @@ struct FramePlan {
   long long K;
   long long P_pitch;
   size_t off_rec, off_rowcnt, off_rowsum;  // in the zeroed region
-  size_t off_P, off_tilemax, off_rowmax, off_bal;  // in the rest
+  size_t off_P, off_tilemax, off_bal;      // in the rest
   size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
   long long plane_pitch32, plane_pitch16;
   size_t off_copy;                          // aligned copy of an unaligned input (0 if none)
@@ -170,8 +170,6 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     o = align_up(o + size_t(f.P_pitch) * f.H, 1024);
     f.off_tilemax = o;
     o = align_up(o + size_t(f.tiles_x) * f.tiles_y, 256);
-    f.off_rowmax = o;
-    o = align_up(o + size_t(f.tiles_x) * f.H, 256);
     f.off_bal = 0;
     if (balance) {
       f.off_bal = o;
