@@ -816,20 +816,21 @@ struct P3Const {
 };
 
 // t of pixel k of a group (bytes of I in iw, of P in pw; plane pointer tp)
-__device__ __forceinline__ float t_of(int tsrc, const uint32_t* iw, const uint32_t* pw, const void* tp, int k,
+template <int TS>
+__device__ __forceinline__ float t_of(const uint32_t* iw, const uint32_t* pw, const void* tp, int k,
                                       const P3Const& K, const HzKParams& kp) {
-  if (tsrc == TS_P) {
+  if constexpr (TS == TS_P) {
     const float m0 = fmaf(bytef(pw[(3 * k) >> 2], (3 * k) & 3), K.inv[0], K.ninv[0]);
     const float m1 = fmaf(bytef(pw[(3 * k + 1) >> 2], (3 * k + 1) & 3), K.inv[1], K.ninv[1]);
     const float m2 = fmaf(bytef(pw[(3 * k + 2) >> 2], (3 * k + 2) & 3), K.inv[2], K.ninv[2]);
     return fmaxf(fmaf(-kp.omega, fminf(fminf(m0, m1), m2), 1.f), kp.t0);
-  } else if (tsrc == TS_FAST) {
+  } else if constexpr (TS == TS_FAST) {
     const float i0 = bytef(iw[(3 * k) >> 2], (3 * k) & 3);
     const float i1 = bytef(iw[(3 * k + 1) >> 2], (3 * k + 1) & 3);
     const float i2 = bytef(iw[(3 * k + 2) >> 2], (3 * k + 2) & 3);
     const float mu = fmaf(fminf(fminf(i0, i1), i2), K.inv_fast, K.ninv_fast);
     return fmaxf(fmaf(-kp.omega, mu, 1.f), kp.t0);
-  } else if (tsrc == TS_PLANE32) {
+  } else if constexpr (TS == TS_PLANE32) {
     return static_cast<const float*>(tp)[k];
   } else {
     return __half2float(static_cast<const __half*>(tp)[k]);
@@ -844,6 +845,60 @@ __device__ __forceinline__ float jg_of(float vbits, int c, float rt, const P3Con
   float Jg = kp.gamma_is_one ? J : ex2a(kp.gamma_inv * lg2a(J));
   if constexpr (MODE == M_BAL_APPLY) Jg = fminf(Jg * K.gains[c], 1.f);
   return Jg;
+}
+
+// The 16 pixels of one group, with the transmission source TS fixed at
+// compile time; FULL groups (16 pixels inside the frame) skip the edge tests.
+template <int MODE, int TS, bool FULL>
+__device__ __forceinline__ void p3_pixels(const HzJob& jb, const HzKParams& kp, const P3Const& K, int x, int y,
+                                          int nv, const uint32_t (&iw)[12], const uint32_t (&pw)[12],
+                                          const void* tp, float& js0, float& js1, float& js2) {
+  if constexpr (MODE == M_T_ONLY) {
+    uint8_t* trow = static_cast<uint8_t*>(jb.tplane) + (long long)y * jb.t_pitch;
+#pragma unroll
+    for (int k = 0; k < P3_GPX; ++k) {
+      if (FULL || k < nv) {
+        const float t = t_of<TS>(iw, pw, tp, k, K, kp);
+        if (jb.t_half_out) reinterpret_cast<__half*>(trow)[x + k] = __float2half_rn(t);
+        else reinterpret_cast<float*>(trow)[x + k] = t;
+      }
+    }
+  } else {
+    float q[4];
+    uint32_t ow[12];
+#pragma unroll
+    for (int k = 0; k < P3_GPX; ++k) {
+      const float t = (FULL || k < nv) ? t_of<TS>(iw, pw, tp, k, K, kp) : 1.f;
+      const float rt = rcpa(t);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int b = 3 * k + c;
+        const float Jg = jg_of<MODE>(bytef(iw[b >> 2], b & 3), c, rt, K, kp);
+        if constexpr (MODE == M_BAL_SUMS) {
+          if (FULL || k < nv) {
+            if (c == 0) js0 += Jg;
+            else if (c == 1) js1 += Jg;
+            else js2 += Jg;
+          }
+        } else {
+          q[b & 3] = fmaf(Jg, 255.f, MAGIC_RINT);
+          if ((b & 3) == 3) ow[b >> 2] = pack4(q[0], q[1], q[2], q[3]);
+        }
+      }
+    }
+    if constexpr (MODE == M_OUT || MODE == M_BAL_APPLY) {
+      uint8_t* Op = jb.out + (long long)y * jb.out_pitch + 3LL * x;
+      if ((FULL || nv == P3_GPX) && ((reinterpret_cast<uintptr_t>(Op) & 15) == 0)) {
+        uint4* o = reinterpret_cast<uint4*>(Op);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) __stcs(o + k, make_uint4(ow[4 * k], ow[4 * k + 1], ow[4 * k + 2], ow[4 * k + 3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3 * P3_GPX; ++i)
+          if (i < 3 * nv) Op[i] = uint8_t(byte_of(ow, i));
+      }
+    }
+  }
 }
 
 // One reconstruction unit (P3_THREADS groups of 16 pixels) of a frame;
@@ -905,50 +960,19 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
         pw[4 * k] = v.x; pw[4 * k + 1] = v.y; pw[4 * k + 2] = v.z; pw[4 * k + 3] = v.w;
       }
     }
-    if constexpr (MODE == M_T_ONLY) {
-      uint8_t* trow = static_cast<uint8_t*>(jb.tplane) + (long long)y * jb.t_pitch;
-#pragma unroll
-      for (int k = 0; k < P3_GPX; ++k) {
-        if (k < nv) {
-          const float t = t_of(jb.tsrc, iw, pw, tp, k, K, kp);
-          if (jb.t_half_out) reinterpret_cast<__half*>(trow)[x + k] = __float2half_rn(t);
-          else reinterpret_cast<float*>(trow)[x + k] = t;
-        }
+    if (nv == P3_GPX) {
+      switch (jb.tsrc) {
+        case TS_P: p3_pixels<MODE, TS_P, true>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        case TS_FAST: p3_pixels<MODE, TS_FAST, true>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        case TS_PLANE32: p3_pixels<MODE, TS_PLANE32, true>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        default: p3_pixels<MODE, TS_PLANE16, true>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
       }
     } else {
-      float q[4];
-      uint32_t ow[12];
-#pragma unroll
-      for (int k = 0; k < P3_GPX; ++k) {
-        const float t = (k < nv) ? t_of(jb.tsrc, iw, pw, tp, k, K, kp) : 1.f;
-        const float rt = rcpa(t);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int b = 3 * k + c;
-          const float Jg = jg_of<MODE>(bytef(iw[b >> 2], b & 3), c, rt, K, kp);
-          if constexpr (MODE == M_BAL_SUMS) {
-            if (k < nv) {
-              if (c == 0) js0 += Jg;
-              else if (c == 1) js1 += Jg;
-              else js2 += Jg;
-            }
-          } else {
-            q[b & 3] = fmaf(Jg, 255.f, MAGIC_RINT);
-            if ((b & 3) == 3) ow[b >> 2] = pack4(q[0], q[1], q[2], q[3]);
-          }
-        }
-      }
-      if constexpr (MODE == M_OUT || MODE == M_BAL_APPLY) {
-        uint8_t* Op = jb.out + (long long)y * jb.out_pitch + 3LL * x;
-        if (nv == P3_GPX && ((reinterpret_cast<uintptr_t>(Op) & 15) == 0)) {
-          uint4* o = reinterpret_cast<uint4*>(Op);
-#pragma unroll
-          for (int k = 0; k < 3; ++k) __stcs(o + k, make_uint4(ow[4 * k], ow[4 * k + 1], ow[4 * k + 2], ow[4 * k + 3]));
-        } else {
-#pragma unroll
-          for (int i = 0; i < 3 * P3_GPX; ++i)
-            if (i < 3 * nv) Op[i] = uint8_t(byte_of(ow, i));
-        }
+      switch (jb.tsrc) {
+        case TS_P: p3_pixels<MODE, TS_P, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        case TS_FAST: p3_pixels<MODE, TS_FAST, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        case TS_PLANE32: p3_pixels<MODE, TS_PLANE32, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
+        default: p3_pixels<MODE, TS_PLANE16, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
       }
     }
   }
@@ -993,7 +1017,7 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
 
 
 template <int MODE>
-__global__ void __launch_bounds__(P3_THREADS) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+__global__ void __launch_bounds__(P3_THREADS, 5) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   const HzJob& jb = jobs.j[blockIdx.y];
   if ((int)blockIdx.x >= p3_units(jb.W, jb.H)) return;
   p3_unit<MODE>(jb, kp, blockIdx.x);
