@@ -47,7 +47,7 @@ constexpr int HZ_STATUS_DEVICE_TIMEOUT = -6;   // per-frame status: a bounded de
 // Per-frame record, zeroed before each launch that uses it.
 struct __align__(16) HzFrameRec {
   unsigned hist[256];           // histogram of D
-  unsigned done_p1, done_p2, done_p3, launch_done;  // launch_done: first record only
+  unsigned done_pad, done_p2, done_p3, launch_done;  // launch_done: first record only
   int T;                        // threshold level
   int status;
   long long n_above;            // #(D > T)

@@ -1,11 +1,12 @@
 // Device code of the video-mode path:
-//   p1  dark channel tiles: per-channel 2-D patch minima P (Eq. 2), the
-//       histogram of D = min_c P^c and per-tile maxima; the last tile of a
-//       frame derives the threshold level T of the top-K set (Eq. 3).
-//   p2  selection: tiles whose maximum reaches T add the r/g/b sums of
-//       pixels with D > T and per-row tie counts/sums for D == T; the last
-//       tile cuts the ties in raster order and forms A_hat (Eq. 3).
-//   fin airlight finish: override or smoothing across frames, 1/A factors.
+//   p1  dark channel regions: per-channel 2-D patch minima P (Eq. 2), the
+//       histogram of D = min_c P^c and per-region maxima.
+//   p2  selection: every block derives the threshold level T of the top-K
+//       set (Eq. 3) from the frame's histogram; regions whose maximum
+//       reaches T add the r/g/b sums of pixels with D > T and per-row tie
+//       counts/sums for D == T; the last region of a frame cuts the ties in
+//       raster order and forms A_hat (Eq. 3); the last block of the launch
+//       runs the airlight chain (override or smoothing across frames, 1/A).
 //   p3  pointwise reconstruction: t (Eq. 4-5 / dark channel of I/A), J
 //       (Eq. 7), clip, gamma (Eq. 8), optional gray-world balance, rint.
 #pragma once
@@ -74,25 +75,28 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // ------------------------------------------------------------------------
-// p1: one strip x band region of one frame (SW output pixels wide, band_h
-// output rows tall), streamed row by row.
+// p1: one region of one frame: P1_SW output pixels wide (a strip), BH =
+// M (2R + 1) output rows tall (a band).
 //
-//  * Rows of the staged strip (SW + 2 RA pixels, RA = R rounded up to 4)
-//    arrive in shared memory by TMA bulk copies (cp.async.bulk, one per row,
-//    16-byte aligned source span), completed on an mbarrier per buffer.
+//  * Staging: the band's NROWS = BH + 2R (+ padding to whole vHGW blocks)
+//    input rows, SW + 2 RA pixels each (RA = R rounded up to 4), land in
+//    shared memory by bulk copies (cp.async.bulk, one per row issued by its
+//    own thread, a 16-byte aligned span), completed on one mbarrier per
+//    chunk of rows; rows outside the frame hold 0xFF (+inf for minima).
 //  * Vertical minimum: each thread owns one 4-byte column of the staged rows
-//    and runs van Herk / Gil-Werman over blocks of p = 2R + 1 rows in
-//    registers (prefix running minimum, suffix minima of the previous block:
-//    three u16x2 minima per value). The 4 interleaved bytes of a column are
-//    two u16x2 views, w (bytes 1 and 3 in the lanes' high bytes) and w << 8
-//    (bytes 0 and 2); the low bytes are don't-care and never change the high
-//    byte of a lane minimum.
-//  * Horizontal minimum: per run of 20 output pixels, each pixel becomes an
+//    and runs van Herk / Gil-Werman over blocks of p = 2R + 1 rows (prefix
+//    running minimum, suffix minima of the previous block: three u16x2
+//    minima per value), writing each output block over the input block it
+//    no longer needs. The 4 interleaved bytes of a column are two u16x2
+//    views, w (bytes 1 and 3 in the lanes' high bytes) and w << 8 (bytes 0
+//    and 2); the low bytes are don't-care and never change the high byte of
+//    a lane minimum.
+//  * Horizontal minimum: per (row, 64-pixel segment), each pixel becomes an
 //    RGBX word (one PRMT) split into the same two views, and the window
-//    minimum along pixels is taken by doubling windows on those arrays.
+//    minimum runs as a streaming van Herk / Gil-Werman along the pixels.
 //  * Epilogue: P bytes (RGB) straight to global memory, D = min_c P^c,
-//    warp-private histogram (run-length merged), region maximum; the last
-//    region of a frame derives T, n_above and m_ties (Eq. 3 set).
+//    histograms shared by groups of warps (run-length merged), folded into
+//    the frame's histogram; the region maximum is the highest bin.
 
 constexpr int P1_HSEG = 64;              // output pixels per horizontal item
 constexpr int P1_NSEG = P1_SW / P1_HSEG;  // horizontal items per row
@@ -351,7 +355,7 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MBAR);
   unsigned* whist = reinterpret_cast<unsigned*>(smem + G::OFF_HIST);
   __shared__ unsigned red[32];
-  __shared__ int s_last, s_fail;
+  __shared__ int s_fail;
 
   for (int i = tid; i < G::NHIST * 256; i += G::NT) whist[i] = 0u;
   if (tid == 0) {
@@ -425,39 +429,8 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
     unsigned m = 0;
     for (int w = 0; w < G::NT / 32; ++w) m = max(m, red[w]);
     jb.tilemax[item] = uint8_t(m ? m - 1u : 0u);
-    // one release fence for the block's histogram and maximum (ordered
-    // before it by the barrier), then the region counter
-    __threadfence();
-    const unsigned nitems = unsigned(jb.tiles_x * jb.tiles_y);
-    s_last = (atomicAdd(&jb.rec->done_p1, 1u) == nitems - 1u);
-  }
-  __syncthreads();
-  if (tid == 0)
+    // every wait on the chunk barriers ended before the phase-1 barrier
     for (int c = 0; c < G::NCH; ++c) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar + c)));
-  if (!s_last) return false;
-  __threadfence();
-  // suffix counts S(v) = #(D >= v); T = max{v : S(v) >= K}, scanned by the
-  // first 256 threads
-  const unsigned hv = (tid < 256) ? __ldcg(&jb.rec->hist[255 - tid]) : 0u;
-  unsigned h = hv;
-  const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned t = __shfl_up_sync(0xffffffffu, h, o);
-    if (lane >= o) h += t;
-  }
-  if (lane == 31 && wid < 8) red[wid] = h;
-  __syncthreads();
-  if (tid < 256) {
-    unsigned add = 0;
-    for (int w = 0; w < wid; ++w) add += red[w];
-    const unsigned incl = h + add, excl = incl - hv;
-    const unsigned long long K = (unsigned long long)jb.K;
-    if (incl >= K && excl < K) {
-      jb.rec->T = 255 - tid;
-      jb.rec->n_above = (long long)excl;
-      jb.rec->m_ties = (long long)(K - excl);
-    }
   }
   return true;
 }
@@ -473,7 +446,9 @@ __global__ void __launch_bounds__(P1S<R>::NT) k_p1(const __grid_constant__ HzJob
 
 // ------------------------------------------------------------------------
 // p2: candidate tiles of the selection, and the raster-order cut.
-__device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
+// The frame's cut (last region of the frame): T and n_above from the
+// histogram scan, m = K - n_above ties taken in raster order.
+__device__ void p2_finalize(const HzJob& jb, const HzKParams& kp, int T, unsigned long long n_above) {
   __shared__ unsigned sh[32];
   __shared__ unsigned long long shl[32];
   __shared__ int s_found, s_row, s_cut;
@@ -482,8 +457,12 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp) {
   constexpr int NTH = 256;  // k_p2 block
   HzFrameRec* rec = jb.rec;
   const int H = jb.H, W = jb.W;
-  const unsigned m = (unsigned)__ldcg(&rec->m_ties);
-  const int T = __ldcg(&rec->T);
+  const unsigned m = (unsigned)((unsigned long long)jb.K - n_above);
+  if (tid == 0) {
+    rec->T = T;
+    rec->n_above = (long long)n_above;
+    rec->m_ties = (long long)m;
+  }
   // rows before the cut row: ordered scan of the per-row tie counts, one
   // row per thread and pass, stopping at the pass that reaches m
   unsigned base = 0;
@@ -705,11 +684,27 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   const int item = blockIdx.x;
   const int nitems = jb.tiles_x * jb.tiles_y;
   if (item >= nitems) return;
-  __shared__ int s_last, s_all;
+  __shared__ int s_last, s_all, s_T;
+  __shared__ unsigned long long s_above;
+  __shared__ unsigned s_part[8];
   const int tid = threadIdx.x;
   HzFrameRec* rec = jb.rec;
-  const int T = rec->T;
-  if ((int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
+  // T = max{v : #(D >= v) >= K} from the frame's histogram (complete: the
+  // dark-channel launch has ended); thread i holds bin 255 - i
+  if (tid == 0) {
+    s_T = -1;
+    s_above = 0;
+  }
+  const unsigned hv = __ldcg(&rec->hist[255 - tid]);
+  const unsigned incl = block_scan_incl(hv, s_part, nullptr);
+  const unsigned long long K = (unsigned long long)jb.K;
+  if (incl >= K && incl - hv < K) {
+    s_T = 255 - tid;
+    s_above = incl - hv;
+  }
+  __syncthreads();
+  const int T = s_T;
+  if (T >= 0 && (int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
   // counters: thread 0 releases the block's writes (ordered before it by
   // the barrier) with one fence, then counts the block
   __syncthreads();
@@ -720,7 +715,11 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   __syncthreads();
   if (s_last) {
     __threadfence();
-    p2_finalize(jb, kp);  // its record writes are thread 0's
+    if (T >= 0) {
+      p2_finalize(jb, kp, T, s_above);  // its record writes are thread 0's
+    } else if (tid == 0) {
+      rec->status = HZ_STATUS_SELECT_FAILED;  // fewer than K pixels counted
+    }
   }
   if (tid == 0) {
     __threadfence();
