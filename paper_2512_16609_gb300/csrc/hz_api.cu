@@ -160,7 +160,7 @@ static hz_status run_front(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, cudaSt
   {
     // selection; its last block also runs the airlight chain
     LaunchScope ls(c, HZ_K_SELECT, s);
-    k_p2<<<g1, 256, 0, s>>>(jobs, kp);
+    k_p2<<<dim3(P2_BLOCKS, jobs.n), 256, 0, s>>>(jobs, kp);
   }
   HZ_CK(c, cudaGetLastError());
   return HZ_OK;
@@ -593,7 +593,7 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
     HZ_CK(c, cudaStreamWaitEvent(sb, c->ev_dark[k], 0));
     {
       LaunchScope ls(c, HZ_K_SELECT, sb);
-      k_p2<<<dim3(max_tiles(jobs), m), 256, 0, sb>>>(jobs, kp);
+      k_p2<<<dim3(P2_BLOCKS, m), 256, 0, sb>>>(jobs, kp);
     }
     HZ_CK(c, cudaGetLastError());
     HZ_CK(c, cudaEventRecord(c->ev_sel[k], sb));
@@ -1167,7 +1167,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
 #undef HZ_NA_P1
       default: break;
     }
-    k_p2<<<g1, 256, 0, s>>>(jobs, kp);
+    k_p2<<<dim3(P2_BLOCKS, 1), 256, 0, s>>>(jobs, kp);
     if (bal) {
       k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
       k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);

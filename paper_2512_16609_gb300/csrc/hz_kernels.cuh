@@ -681,9 +681,9 @@ __device__ void fin_frames(const HzJobs& jobs, const HzKParams& kp) {
 // chain of all frames (launch counter in the first frame's record).
 __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   const HzJob& jb = jobs.j[blockIdx.y];
-  const int item = blockIdx.x;
   const int nitems = jb.tiles_x * jb.tiles_y;
-  if (item >= nitems) return;
+  const int nb = p2_blocks(nitems);  // blocks of this frame; block b takes regions b, b + nb, ...
+  if ((int)blockIdx.x >= nb) return;
   __shared__ int s_last, s_all, s_T;
   __shared__ unsigned long long s_above;
   __shared__ unsigned s_part[8];
@@ -704,13 +704,15 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   }
   __syncthreads();
   const int T = s_T;
-  if (T >= 0 && (int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
+  if (T >= 0)
+    for (int item = blockIdx.x; item < nitems; item += nb)
+      if ((int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
   // counters: thread 0 releases the block's writes (ordered before it by
   // the barrier) with one fence, then counts the block
   __syncthreads();
   if (tid == 0) {
     __threadfence();
-    s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nitems) - 1u);
+    s_last = (atomicAdd(&rec->done_p2, 1u) == unsigned(nb) - 1u);
   }
   __syncthreads();
   if (s_last) {
@@ -724,7 +726,7 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   if (tid == 0) {
     __threadfence();
     unsigned total = 0;
-    for (int f = 0; f < jobs.n; ++f) total += unsigned(jobs.j[f].tiles_x * jobs.j[f].tiles_y);
+    for (int f = 0; f < jobs.n; ++f) total += unsigned(p2_blocks(jobs.j[f].tiles_x * jobs.j[f].tiles_y));
     s_all = (atomicAdd(&jobs.j[0].rec->launch_done, 1u) == total - 1u);
   }
   __syncthreads();
