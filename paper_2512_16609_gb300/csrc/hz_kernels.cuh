@@ -395,6 +395,22 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
     return false;
   }
 
+  // staged pixels outside the frame (the halos of the first and last strip)
+  // become +inf in the vertical minima, so that only segments crossing the
+  // right edge (partial output) take the masked path of the horizontal pass
+  {
+    const int nlo = 3 * min(G::EW, max(0, -xs));        // bytes of pixels x < 0
+    const int hi0 = 3 * max(0, min(G::EW, W - xs));     // first byte of pixels x >= W
+    const int per = nlo + (3 * G::EW - hi0);
+    if (per > 0) {
+      for (int i = tid; i < bh * per; i += G::NT) {
+        const int k = i / per, b = i - k * per;
+        smem[k * G::SLOT + G::S0 + (b < nlo ? b : hi0 + (b - nlo))] = 0xffu;
+      }
+      __syncthreads();
+    }
+  }
+
   // ---- phase 2: horizontal minima, (row, 64-pixel segment) per thread ----
   unsigned* hw = whist + ((tid >> 5) % G::NHIST) * 256;
   for (int it = tid; it < bh * P1_NSEG; it += G::NT) {
@@ -403,7 +419,7 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
     if (xo >= W) continue;
     const uint4* vq = reinterpret_cast<const uint4*>(smem + k * G::SLOT + G::IB0 + 3 * P1_HSEG * seg);
     const int sp0 = xo - R;  // image pixel of element 0
-    const bool edge = (sp0 < 0) || (sp0 + G::NIN > W);
+    const bool edge = xo + P1_HSEG > W;
     uint4* Pp = reinterpret_cast<uint4*>(jb.P + (long long)(y0 + k) * jb.P_pitch + 3LL * xo);
     uint8_t* Dp = jb.Dout ? jb.Dout + (long long)(y0 + k) * jb.D_pitch + xo : nullptr;
     if (edge || Dp) p1_hitem<R, true>(vq, sp0, W, min(P1_HSEG, W - xo), Pp, Dp, hw);
