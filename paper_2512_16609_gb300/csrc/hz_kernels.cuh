@@ -174,30 +174,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity) 
 }
 
 // Stage every row of the band. Rows outside the frame (or past the last
-// needed row) are filled with 0xFF (+inf for minima) by the whole block;
-// every other row is one bulk copy (16-byte aligned span) issued by its own
-// thread, which arrives on its chunk's barrier with the copy's byte count
-// (barrier count = rows per chunk). Staged byte 0 of every row sits at slot
-// byte S0: frames are 16-byte aligned with a pitch that is a multiple of 16,
-// so every row's copy lands at the same offset.
+// needed row) are filled with 0xFF (+inf for minima) by the whole block
+// (p1_fill_rows); every other row is one bulk copy (16-byte aligned span)
+// issued by a lane of warp 0 (p1_issue_rows), which arrives on its chunk's
+// barrier with the copy's byte count (barrier count = rows per chunk).
+// Staged byte 0 of every row sits at slot byte S0: frames are 16-byte
+// aligned with a pitch that is a multiple of 16, so every row's copy lands at
+// the same offset.
 template <int R>
-__device__ __forceinline__ void p1_stage_band(const HzJob& jb, int ya, int nrows_need, int xs, int xa, int xb,
-                                              unsigned char* smem, uint64_t* mbar) {
+__device__ __forceinline__ void p1_row_range(const HzJob& jb, int ya, int nrows_need, int& k_lo, int& k_hi) {
+  constexpr int NR = P1S<R>::NCH * P1S<R>::CH;
+  k_lo = min(NR, max(0, -ya));
+  k_hi = max(k_lo, min(NR, min(jb.H - ya, nrows_need)));
+}
+
+template <int R>
+__device__ __forceinline__ void p1_fill_rows(const HzJob& jb, int ya, int nrows_need, bool empty, unsigned char* smem) {
   using G = P1S<R>;
   constexpr int NR = G::NCH * G::CH;
-  const int tid = threadIdx.x;
-  // rows [0, k_lo) and [k_hi, NR) hold no frame data
-  const int k_lo = min(NR, max(0, -ya));
-  const int k_hi = max(k_lo, min(NR, min(jb.H - ya, nrows_need)));
-  const bool empty = xa >= xb;
+  int k_lo, k_hi;
+  p1_row_range<R>(jb, ya, nrows_need, k_lo, k_hi);
   for (int k = 0; k < NR; ++k) {
     if (k == k_lo && !empty) k = k_hi;
     if (k >= NR) break;
     uint32_t* row = reinterpret_cast<uint32_t*>(smem + k * G::SLOT);
-    for (int q = tid; q < G::SLOT / 4; q += G::NT) row[q] = 0xffffffffu;
+    for (int q = threadIdx.x; q < G::SLOT / 4; q += G::NT) row[q] = 0xffffffffu;
   }
-  if (tid < NR) {
-    const int k = tid, c = k / G::CH;
+}
+
+template <int R>
+__device__ __forceinline__ void p1_issue_rows(const HzJob& jb, int ya, int nrows_need, int xs, int xa, int xb,
+                                              unsigned char* smem, uint64_t* mbar, int lane) {
+  using G = P1S<R>;
+  constexpr int NR = G::NCH * G::CH;
+  int k_lo, k_hi;
+  p1_row_range<R>(jb, ya, nrows_need, k_lo, k_hi);
+  const bool empty = xa >= xb;
+  for (int k = lane; k < NR; k += 32) {
+    const int c = k / G::CH;
     unsigned bytes = 0;
     const void* src = nullptr;
     unsigned char* dst = nullptr;
@@ -357,15 +371,20 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
   __shared__ unsigned red[32];
   __shared__ int s_fail;
 
-  for (int i = tid; i < G::NHIST * 256; i += G::NT) whist[i] = 0u;
-  if (tid == 0) {
-    s_fail = 0;
-    for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  // warp 0 starts the copies first; the rest of the block clears the
+  // histograms and fills the rows that hold no frame data meanwhile
+  if (tid < 32) {
+    if (tid == 0) {
+      s_fail = 0;
+      for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    p1_issue_rows<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar, tid);
   }
-  __syncthreads();
-  p1_stage_band<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar);
-  __syncthreads();  // +inf fills visible
+  for (int i = tid; i < G::NHIST * 256; i += G::NT) whist[i] = 0u;
+  p1_fill_rows<R>(jb, ya, nrows_need, xa >= xb, smem);
+  __syncthreads();  // barriers initialised, +inf fills and cleared histograms visible
 
   // ---- phase 1: vertical minima, in place, as the chunks land -----------
   {
