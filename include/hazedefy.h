@@ -298,6 +298,35 @@ hz_status hz_get_profile(hz_ctx* ctx, hz_profile* out, int reset);
 hz_status hz_set_wave_bytes(hz_ctx* ctx, size_t bytes);
 hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
 
+/* Wave-size autotuner (no counterpart in the paper): runs the given batch
+ * (layout and rules as for hz_dehaze_batch, which it calls) at each
+ * candidate wave size, 8, 16, 32, 64, 128, 192 and 256 MiB, two untimed and
+ * three timed runs each (CUDA events on cuda_stream), and keeps the fastest
+ * as the context's wave size. Every run starts from the stream states at
+ * entry, which are restored at the end, so the outputs equal those of one
+ * hz_dehaze_batch call and the states are left unchanged. *best_bytes (optional) receives the chosen size; ms_per_candidate
+ * (optional, n_candidates >= 7 entries) the mean milliseconds per batch of
+ * each candidate. Synchronises the stream. Errors: HZ_EINVAL for a bad frame
+ * list or a short ms_per_candidate, HZ_ECUDA / HZ_ENOMEM from the runs (the
+ * previous wave size is kept). */
+hz_status hz_autotune_wave_bytes(hz_ctx* ctx, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
+                                 size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates);
+
+/* Graph replay (no counterpart in the paper): when on, hz_dehaze_batch and
+ * device-buffer hz_dehaze_video calls without info output are keyed by a
+ * signature (frame pointers, sizes, pitches, stream ids, flags, parameters,
+ * wave size, scratch addresses). The second call with a signature is
+ * captured into a CUDA graph on a stream of the context (nothing runs while
+ * capturing) and launched on the caller's stream; later calls with it replay
+ * the graph, skipping the host-side planning and launches. Up to 8
+ * signatures keep graphs (least recently used evicted). Results are identical
+ * to direct calls; per-stream state advances the same way. Calls with info
+ * output, calls while profiling is on, and captures that fail run directly.
+ * Turning replay off frees the graphs. */
+hz_status hz_set_graph_replay(hz_ctx* ctx, int on);
+/* Graphs captured and replays done since the context was created. */
+hz_status hz_get_graph_stats(hz_ctx* ctx, uint64_t* captures, uint64_t* replays);
+
 /* --------------------------------------------- allocation-free frame -- */
 /* The paper has no counterpart to this call; it exists for callers that are
  * not allowed to allocate device memory at run time: plug-ins that run inside

@@ -143,6 +143,9 @@ _SIGS = {
     "hz_reset_server_stats": (C.c_int, [_P]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
     "hz_set_wave_bytes": (C.c_int, [_P, _SZ]),
+    "hz_autotune_wave_bytes": (C.c_int, [_P, _P, _I, _P, C.POINTER(_SZ), C.POINTER(C.c_float), _I]),
+    "hz_set_graph_replay": (C.c_int, [_P, C.c_int]),
+    "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "hz_get_wave_bytes": (C.c_int, [_P, C.POINTER(_SZ)]),
     "hz_get_profile": (C.c_int, [_P, C.POINTER(hz_profile), C.c_int]),
 }
@@ -276,18 +279,7 @@ def hz_dehaze_video(ctx, inp, out, stream_id: int = -1, flags: int = 0, stream=N
 
 def hz_dehaze_batch(ctx, frames, outs, stream_ids=None, guided=None, stream=None, want_info: bool = False):
     n = len(frames)
-    descs = (hz_frame_desc * max(n, 1))()
-    for i, (a, b) in enumerate(zip(frames, outs)):
-        pi, W, H, ip = frame_args(a)
-        po, _, _, op = frame_args(b)
-        descs[i].in_ = pi.value
-        descs[i].in_pitch = ip
-        descs[i].out = po.value
-        descs[i].out_pitch = op
-        descs[i].W = W
-        descs[i].H = H
-        descs[i].stream_id = -1 if stream_ids is None else int(stream_ids[i])
-        descs[i].flags = HZ_GUIDED if (guided is not None and guided[i]) else 0
+    descs = _descs(frames, outs, stream_ids, guided)
     infos = (hz_frame_info * max(n, 1))() if want_info else None
     st = lib().hz_dehaze_batch(ctx, descs, n, _stream_ptr(stream), infos)
     _check(st, ctx, "hz_dehaze_batch")
@@ -417,6 +409,47 @@ def params(**kw) -> hz_params:
 def hz_set_wave_bytes(ctx, nbytes: int):
     """Input bytes per wave of the video path (0 = default)."""
     return _check(lib().hz_set_wave_bytes(ctx, int(nbytes)), ctx, "hz_set_wave_bytes")
+
+
+TUNE_WAVE_MIB = (8, 16, 32, 64, 128, 192, 256)
+
+
+def _descs(frames, outs, stream_ids=None, guided=None):
+    n = len(frames)
+    descs = (hz_frame_desc * max(n, 1))()
+    for i, (a, b) in enumerate(zip(frames, outs)):
+        pi, W, H, ip = frame_args(a)
+        po, _, _, op = frame_args(b)
+        descs[i].in_ = pi.value
+        descs[i].in_pitch = ip
+        descs[i].out = po.value
+        descs[i].out_pitch = op
+        descs[i].W = W
+        descs[i].H = H
+        descs[i].stream_id = -1 if stream_ids is None else int(stream_ids[i])
+        descs[i].flags = HZ_GUIDED if (guided is not None and guided[i]) else 0
+    return descs
+
+
+def hz_autotune_wave_bytes(ctx, frames, outs, stream_ids=None, guided=None, stream=None):
+    """Pick the fastest wave size for this batch; returns (bytes, {MiB: ms})."""
+    descs = _descs(frames, outs, stream_ids, guided)
+    best = _SZ(0)
+    ms = (C.c_float * len(TUNE_WAVE_MIB))()
+    _check(lib().hz_autotune_wave_bytes(ctx, descs, len(frames), _stream_ptr(stream), C.byref(best), ms,
+                                        len(TUNE_WAVE_MIB)), ctx, "hz_autotune_wave_bytes")
+    return int(best.value), {mb: float(ms[i]) for i, mb in enumerate(TUNE_WAVE_MIB)}
+
+
+def hz_set_graph_replay(ctx, on: bool):
+    return _check(lib().hz_set_graph_replay(ctx, 1 if on else 0), ctx, "hz_set_graph_replay")
+
+
+def hz_get_graph_stats(ctx):
+    """(graphs captured, replays) since the context was created."""
+    a, b = C.c_uint64(0), C.c_uint64(0)
+    _check(lib().hz_get_graph_stats(ctx, C.byref(a), C.byref(b)), ctx, "hz_get_graph_stats")
+    return int(a.value), int(b.value)
 
 
 def hz_get_wave_bytes(ctx) -> int:

@@ -406,6 +406,7 @@ extern "C" hz_status hz_create(const hz_params* p, int device, size_t mem_budget
          cudaEventCreateWithFlags(&c->ev_dark[q], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_sel[q], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_free[q], cudaEventDisableTiming) == cudaSuccess;
+  if (ok) ok = cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking) == cudaSuccess;
   if (ok)
     ok = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_end, cudaEventDisableTiming) == cudaSuccess;
@@ -449,6 +450,9 @@ extern "C" hz_status hz_destroy(hz_ctx* c) {
     if (c->ev_sel[q]) cudaEventDestroy(c->ev_sel[q]);
     if (c->ev_free[q]) cudaEventDestroy(c->ev_free[q]);
   }
+  for (auto& g : c->gcache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->gs) cudaStreamDestroy(c->gs);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
   if (c->rec_pinned) cudaFreeHost(c->rec_pinned);
@@ -636,6 +640,97 @@ static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStr
   return read_infos(c, lp, n, s, infos, bal);
 }
 
+// Signature of a device-buffer call for graph replay: the call's own bytes,
+// the parameters, the wave size and the scratch base addresses the captured
+// launches refer to.
+static std::string call_key(const hz_ctx* c, const void* a, size_t na, const void* b, size_t nb) {
+  std::string k;
+  const uintptr_t bases[2] = {uintptr_t(c->arena.base), uintptr_t(c->stage.base)};
+  k.append(reinterpret_cast<const char*>(&c->prm), sizeof c->prm);
+  k.append(reinterpret_cast<const char*>(&c->wave_bytes), sizeof c->wave_bytes);
+  k.append(reinterpret_cast<const char*>(bases), sizeof bases);
+  k.append(static_cast<const char*>(a), na);
+  if (b) k.append(static_cast<const char*>(b), nb);
+  return k;
+}
+
+// Runs body(stream) on s directly or through the context's graph cache:
+// the first call with a signature runs directly (and sizes the scratch), the
+// second is captured on gs (nothing runs while capturing) and its graph
+// launched on s, later ones replay it. A capture that fails falls back to
+// the direct call.
+template <class F>
+static hz_status graph_call(hz_ctx* c, cudaStream_t s, const std::string& key, F&& body) {
+  bool prof;
+  {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    prof = c->prof;
+  }
+  if (!c->graphs || prof) return body(s);
+  auto add_launches = [c](const uint64_t* l) {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    for (int k = 0; k < HZ_K_COUNT; ++k) c->launches[k] += l[k];
+  };
+  hz_ctx::GraphEntry* e = nullptr;
+  for (auto& g : c->gcache)
+    if (g.key == key) e = &g;
+  if (e && e->exec) {
+    e->last_use = ++c->g_tick;
+    HZ_CK(c, cudaGraphLaunch(e->exec, s));
+    add_launches(e->launches);
+    ++c->g_replays;
+    return HZ_OK;
+  }
+  if (!e) {  // first sight: remember it, run directly
+    if ((int)c->gcache.size() >= GRAPH_CACHE) {
+      auto lru = c->gcache.begin();
+      for (auto it = c->gcache.begin(); it != c->gcache.end(); ++it)
+        if (it->last_use < lru->last_use) lru = it;
+      if (lru->exec) cudaGraphExecDestroy(lru->exec);
+      c->gcache.erase(lru);
+    }
+    hz_ctx::GraphEntry g;
+    g.key = key;
+    g.last_use = ++c->g_tick;
+    c->gcache.push_back(std::move(g));
+    return body(s);
+  }
+  // second sight: capture
+  uint64_t before[HZ_K_COUNT], captured[HZ_K_COUNT];
+  {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    std::memcpy(before, c->launches, sizeof before);
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const hz_status st = body(c->gs);
+    ok = (cudaStreamEndCapture(c->gs, &g) == cudaSuccess) && st == HZ_OK && g;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    for (int k = 0; k < HZ_K_COUNT; ++k) {
+      captured[k] = c->launches[k] - before[k];
+      c->launches[k] = before[k];  // nothing ran while capturing
+    }
+  }
+  if (!ok) {
+    cudaGetLastError();
+    c->err.clear();
+    return body(s);
+  }
+  e->exec = ex;
+  std::memcpy(e->launches, captured, sizeof captured);
+  e->last_use = ++c->g_tick;
+  ++c->g_captures;
+  HZ_CK(c, cudaGraphLaunch(e->exec, s));
+  add_launches(e->launches);
+  return HZ_OK;
+}
+
 extern "C" hz_status hz_dehaze_frame(hz_ctx* c, int32_t stream_id, const uint8_t* in, int32_t W, int32_t H,
                                      size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
                                      hz_frame_info* info) {
@@ -706,7 +801,13 @@ extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
-  HZ_TRY(run_batch(c, frames, n, s, infos, nullptr, nullptr));
+  if (infos) {
+    HZ_TRY(run_batch(c, frames, n, s, infos, nullptr, nullptr));
+  } else {
+    const char tag[] = "batch";
+    const std::string key = call_key(c, tag, sizeof tag, frames, sizeof(hz_frame_desc) * size_t(n));
+    HZ_TRY(graph_call(c, s, key, [&](cudaStream_t st) { return run_batch(c, frames, n, st, nullptr, nullptr, nullptr); }));
+  }
   return mark_done(c, s);
 }
 
@@ -728,19 +829,25 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
   // the smoothing chain runs through the stream's state, or a call-local one
-  HzStreamState* chain = nullptr;
-  if (stream_id < 0) {
-    chain = c->states + MAX_STREAMS;
-    HZ_CK(c, cudaMemsetAsync(chain, 0, sizeof(HzStreamState), s));
-  }
+  HzStreamState* chain = (stream_id < 0) ? c->states + MAX_STREAMS : nullptr;
   if (!(flags & HZ_IO_HOST)) {
     std::vector<hz_frame_desc> fr(n_frames);
     for (int f = 0; f < n_frames; ++f)
       fr[f] = hz_frame_desc{in + size_t(f) * in_frame_stride, in_pitch, out + size_t(f) * out_frame_stride,
                             out_pitch, W, H, stream_id, 0u};
-    HZ_TRY(video_device(c, fr.data(), n_frames, s, infos, chain));
+    auto body = [&](cudaStream_t st) -> hz_status {
+      if (chain) HZ_CK(c, cudaMemsetAsync(chain, 0, sizeof(HzStreamState), st));
+      return video_device(c, fr.data(), n_frames, st, infos, chain);
+    };
+    if (infos) {
+      HZ_TRY(body(s));
+    } else {
+      const char tag[] = "video";
+      HZ_TRY(graph_call(c, s, call_key(c, tag, sizeof tag, fr.data(), sizeof(hz_frame_desc) * fr.size()), body));
+    }
     return mark_done(c, s);
   }
+  if (chain) HZ_CK(c, cudaMemsetAsync(chain, 0, sizeof(HzStreamState), s));
   // host buffers: waves of frames staged through HOSTIO_BUFS device buffer
   // pairs; the H2D copy of wave k+1 (copy_in), the compute of wave k (s) and
   // the D2H copy of wave k-1 (copy_out) overlap, so both link directions stay
@@ -990,6 +1097,95 @@ extern "C" hz_status hz_set_wave_bytes(hz_ctx* c, size_t bytes) {
 extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
   if (!c || !bytes) return HZ_EINVAL;
   *bytes = c->wave_bytes;
+  return HZ_OK;
+}
+
+// Wave-size autotuner: times the batch at each candidate wave size (two
+// untimed and three timed runs, CUDA events on the caller's stream) and keeps
+// the fastest. Every run starts from the stream states saved at entry, which
+// are restored at the end: the tuning leaves no trace beyond the outputs,
+// which equal those of one ordinary call.
+static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256};
+
+extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
+                                            size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates) {
+  if (!c) return HZ_EINVAL;
+  if (n <= 0 || !frames) return fail(c, HZ_EINVAL, "bad frame list");
+  for (int i = 0; i < n; ++i) {
+    HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
+                       frames[i].out_pitch, true));
+    HZ_TRY(check_stream_id(c, frames[i].stream_id));
+  }
+  constexpr int NCAND = int(sizeof TUNE_WAVE_MIB / sizeof TUNE_WAVE_MIB[0]);
+  if (ms_per_candidate && n_candidates < NCAND) return fail(c, HZ_EINVAL, "ms_per_candidate holds fewer than %d", NCAND);
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  const size_t sbytes = sizeof(HzStreamState) * (MAX_STREAMS + 1);
+  void* saved = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HZ_CK(c, cudaMalloc(&saved, sbytes));
+  hz_status st = HZ_OK;
+  const size_t keep = c->wave_bytes;
+  size_t best = keep;
+  float best_ms = -1.f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemcpyAsync(saved, c->states, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    st = fail(c, HZ_ECUDA, "autotune setup failed");
+  // every run starts from the saved states (a 48-byte-per-stream copy)
+  auto one_run = [&]() -> hz_status {
+    if (cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(c, HZ_ECUDA, "restoring stream states failed");
+    return run_batch(c, frames, n, s, nullptr, nullptr, nullptr);
+  };
+  for (int k = 0; k < NCAND && st == HZ_OK; ++k) {
+    c->wave_bytes = TUNE_WAVE_MIB[k] << 20;
+    for (int r = 0; r < 2 && st == HZ_OK; ++r) st = one_run();
+    if (st == HZ_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(c, HZ_ECUDA, "event record failed");
+    for (int r = 0; r < 3 && st == HZ_OK; ++r) st = one_run();
+    float ms = 0.f;
+    if (st == HZ_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = fail(c, HZ_ECUDA, "event timing failed");
+    if (st != HZ_OK) break;
+    ms /= 3.f;
+    if (ms_per_candidate) ms_per_candidate[k] = ms;
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c->wave_bytes;
+    }
+  }
+  if (saved && cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess && st == HZ_OK)
+    st = fail(c, HZ_ECUDA, "restoring stream states failed");
+  cudaStreamSynchronize(s);
+  if (saved) cudaFree(saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->wave_bytes = (st == HZ_OK) ? best : keep;
+  if (best_bytes) *best_bytes = c->wave_bytes;
+  if (st != HZ_OK) return st;
+  return mark_done(c, s);
+}
+
+extern "C" hz_status hz_set_graph_replay(hz_ctx* c, int on) {
+  if (!c) return HZ_EINVAL;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->graphs = on != 0;
+  if (!c->graphs) {
+    cudaSetDevice(c->device);
+    for (auto& g : c->gcache)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->gcache.clear();
+  }
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_graph_stats(hz_ctx* c, uint64_t* captures, uint64_t* replays) {
+  if (!c) return HZ_EINVAL;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  if (captures) *captures = c->g_captures;
+  if (replays) *replays = c->g_replays;
   return HZ_OK;
 }
 

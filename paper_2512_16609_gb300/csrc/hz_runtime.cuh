@@ -28,6 +28,7 @@ struct Arena {
 };
 
 constexpr size_t DEFAULT_WAVE_BYTES = size_t(20) << 20;  // input bytes per wave of frames
+constexpr int GRAPH_CACHE = 8;                            // call signatures with graphs per context
 constexpr int HOSTIO_BUFS = 3;                            // staging buffer pairs of host-buffer calls
 constexpr size_t HOSTIO_WAVE_BYTES = size_t(24) << 20;    // input bytes per staged wave
 
@@ -55,6 +56,18 @@ struct hz_ctx {
   hz::HzFrameRec* rec_pinned = nullptr;  // pinned, rec_pinned_cap records
   size_t rec_pinned_cap = 0;
   size_t wave_bytes = hz::DEFAULT_WAVE_BYTES;  // input bytes per wave
+  // graph replay of repeated identical device-buffer calls: the second call
+  // with a signature is captured on gs, later ones replay the graph
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;         // null: seen once, not captured yet
+    uint64_t launches[HZ_K_COUNT] = {0};    // kernel launches the graph holds, per class
+    uint64_t last_use = 0;
+  };
+  bool graphs = false;
+  cudaStream_t gs = nullptr;
+  std::vector<GraphEntry> gcache;           // at most GRAPH_CACHE entries, least recently used evicted
+  uint64_t g_tick = 0, g_captures = 0, g_replays = 0;
   // stream table
   std::mutex smu;
   int stream_open[hz::MAX_STREAMS] = {0};
