@@ -206,32 +206,72 @@ def run_reference(args):
     return 0
 
 
-WAVE_MB_SWEEP = (12.0, 24.0, 48.0, 72.0, 96.0, 144.0, 192.0)
-
-
 def tune_wave_bytes(hzp, ctx, inp, out, choice):
-    """Set the library's wave size: the given MiB, or the fastest of a short
-    sweep (2 untimed + 3 timed calls per size, before the timed region)."""
-    import torch
+    """Set the library's wave size: the given MiB, or the library autotuner's
+    pick for this workload (hz_autotune_wave_bytes: every candidate timed on
+    the step's frames, before the timed region)."""
     if choice != "auto":
         hzp.hz_set_wave_bytes(ctx, int(float(choice) * (1 << 20)))
         return {"wave_mb": float(choice), "sweep": None}
-    sweep = {}
-    for mb in WAVE_MB_SWEEP:
-        hzp.hz_set_wave_bytes(ctx, int(mb * (1 << 20)))
-        for _ in range(2):
-            hzp.hz_dehaze_video(ctx, inp, out)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            hzp.hz_dehaze_video(ctx, inp, out)
-        e1.record()
-        torch.cuda.synchronize()
-        sweep[mb] = round(e0.elapsed_time(e1) / 3, 4)
-    best = min(sweep, key=sweep.get)
-    hzp.hz_set_wave_bytes(ctx, int(best * (1 << 20)))
-    return {"wave_mb": best, "sweep": {f"{k:g}": v for k, v in sweep.items()}}
+    frames = [inp[f] for f in range(inp.shape[0])]
+    outs = [out[f] for f in range(out.shape[0])]
+    best, table = hzp.hz_autotune_wave_bytes(ctx, frames, outs)
+    return {"wave_mb": best / (1 << 20), "sweep_ms": {str(k): round(v, 4) for k, v in table.items()},
+            "tuner": "hz_autotune_wave_bytes"}
+
+
+BATCH_SPECS = hazegen.mixed_batch_specs(16, 100)  # 16 each of 854x480, 1280x720, 1920x1080, 3840x2160
+
+
+def _render_spec(spec):
+    W_, H_, seed, beta = spec
+    return hazegen.make_frame(W_, H_, seed=seed, beta=beta)
+
+
+def make_batch_inputs(nproc):
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(nproc, 16)) as pool:
+        return pool.map(_render_spec, BATCH_SPECS)
+
+
+def run_batch_mixed(hzp, dev, frames, reps=10):
+    """The mixed-size batch (64 frames, 187.2 Mpx): one hz_dehaze_batch call
+    per step on device-resident frames, wave size from the library autotuner,
+    graph replay on; CUDA events on the launching stream, three warm-up
+    calls, inputs (0.56 GB) larger than L2."""
+    import torch
+    ctx = hzp.hz_create(hzp.params(), dev.index)
+    try:
+        ins = [torch.from_numpy(f).to(dev) for f in frames]
+        outs = [torch.empty_like(t) for t in ins]
+        best, table = hzp.hz_autotune_wave_bytes(ctx, ins, outs)
+        hzp.hz_set_graph_replay(ctx, True)
+        stream = torch.cuda.current_stream(dev)
+        res = {}
+        for mode in ("graph", "direct"):
+            hzp.hz_set_graph_replay(ctx, mode == "graph")
+            for _ in range(3):
+                hzp.hz_dehaze_batch(ctx, ins, outs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                hzp.hz_dehaze_batch(ctx, ins, outs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[mode] = e0.elapsed_time(e1) / reps
+        caps, replays = hzp.hz_get_graph_stats(ctx)
+        npx = sum(w * h for (w, h, _, _) in BATCH_SPECS)
+        ms = res["graph"]
+        return {"workload": "64 frames: 16 each of 854x480, 1280x720, 1920x1080, 3840x2160, beta U(0.5,1.5), "
+                            "patch 15, one hz_dehaze_batch call",
+                "ms_per_batch": ms, "frames_per_s": 64 / (ms / 1e3), "mpix_s": npx / (ms / 1e3) / 1e6,
+                "hbm_effective_GBps": npx * ALG_BYTES_PER_PX / (ms / 1e3) / 1e9,
+                "ms_per_batch_without_graph": res["direct"], "wave_mb": best / (1 << 20),
+                "tuner_ms": {str(k): round(v, 4) for k, v in table.items()},
+                "graphs_captured": caps, "graph_replays": replays, "reps": reps}
+    finally:
+        hzp.hz_destroy(ctx)
 
 
 def main():
@@ -245,7 +285,9 @@ def main():
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="length of the served-streams measurement (0 skips it)")
     ap.add_argument("--wave-mb", default="auto",
-                    help="input MiB per wave of frames, or 'auto' to pick the fastest of a short sweep")
+                    help="input MiB per wave of frames, or 'auto' for the library autotuner's pick")
+    ap.add_argument("--no-graphs", action="store_true", help="time direct calls instead of graph replay")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
     ap.add_argument("--frames", type=int, default=300,
                     help="frames per step; only profiling runs change it from the 300-frame workload")
     args = ap.parse_args()
@@ -260,6 +302,9 @@ def main():
     served_inputs = None
     if args.served_seconds > 0 and rank == 0 and ws == 1:
         served_inputs = make_served_inputs(nproc)
+    batch_inputs = None
+    if not args.no_batch and rank == 0 and ws == 1:
+        batch_inputs = make_batch_inputs(nproc)
 
     import torch
     import __graft_entry__ as G
@@ -284,6 +329,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     tuning = tune_wave_bytes(hzp, ctx, inp, out, args.wave_mb)
+    hzp.hz_set_graph_replay(ctx, not args.no_graphs)
     for _ in range(max(3, args.warmup)):
         hzp.hz_dehaze_video(ctx, inp, out)
     torch.cuda.synchronize()
@@ -350,6 +396,10 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(hzp, ctx, frames_np, out, dev, args.steps, ws, barrier)
 
+    batch = None
+    if batch_inputs is not None:
+        batch = run_batch_mixed(hzp, dev, batch_inputs)
+
     served = None
     if served_inputs is not None:
         served = run_served(hzp, dev, served_inputs, args.served_seconds)
@@ -364,7 +414,7 @@ def main():
     hzp.hz_destroy(ctx)
     if rank == 0:
         emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-             launches, clocks, served, tuning)
+             launches, clocks, served, tuning, batch, graphs=not args.no_graphs)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -535,7 +585,7 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
 
 
 def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-         launches, clocks, served=None, tuning=None):
+         launches, clocks, served=None, tuning=None, batch=None, graphs=False):
     if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -543,7 +593,7 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames": F, "W": W, "H": H,
                        "l2": "inputs 1.87 GB per step > L2, no flush", "parallelism": f"replicas{ws}",
-                       "wave_mb": tuning["wave_mb"] if tuning else None},
+                       "wave_mb": tuning["wave_mb"] if tuning else None, "graph_replay": graphs},
             "tuning": tuning,
             "mpix_s": value * W * H / 1e6,
             "hbm_effective": {"bytes_per_px": ALG_BYTES_PER_PX,
@@ -559,6 +609,7 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "serving": served,
+            "batch_mixed": batch,
         }
         print(json.dumps(line), flush=True)
 
