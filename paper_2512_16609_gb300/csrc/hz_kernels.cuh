@@ -113,7 +113,8 @@ struct P1S {
   static constexpr int RA = (R + 3) & ~3;
   static constexpr int EW = P1_SW + 2 * RA;                     // staged pixels
   static constexpr int NWC = 3 * EW / 4;                        // staged 4-byte columns
-  static constexpr int NT = ((NWC + 31) / 32) * 32;             // threads
+  static constexpr int NTC = ((NWC + 31) / 32) * 32;            // compute threads
+  static constexpr int NT = NTC + 32;                           // + one producer warp (row copies)
   static constexpr int SLOT = 16 * (((3 * EW + 48 + 15) / 16) | 1);  // bytes per staged row (16 x odd)
   static constexpr int S0 = 16 + ((-3 * RA) & 15);              // slot byte of staged byte 0
   static constexpr int IB0 = (S0 + 3 * (RA - R)) & ~15;         // item chunk base (+192 per segment)
@@ -174,10 +175,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity) 
 }
 
 // Stage every row of the band. Rows outside the frame (or past the last
-// needed row) are filled with 0xFF (+inf for minima) by the whole block
+// needed row) are filled with 0xFF (+inf for minima) by the compute threads
 // (p1_fill_rows); every other row is one bulk copy (16-byte aligned span)
-// issued by a lane of warp 0 (p1_issue_rows), which arrives on its chunk's
-// barrier with the copy's byte count (barrier count = rows per chunk).
+// issued by a lane of the producer warp (p1_issue_rows), which arrives on its
+// chunk's barrier with the copy's byte count (barrier count = rows per
+// chunk). Issuing can stall for thousands of cycles when the copy engine is
+// busy, so only the producer warp waits for it.
 // Staged byte 0 of every row sits at slot byte S0: frames are 16-byte
 // aligned with a pitch that is a multiple of 16, so every row's copy lands at
 // the same offset.
@@ -198,7 +201,7 @@ __device__ __forceinline__ void p1_fill_rows(const HzJob& jb, int ya, int nrows_
     if (k == k_lo && !empty) k = k_hi;
     if (k >= NR) break;
     uint32_t* row = reinterpret_cast<uint32_t*>(smem + k * G::SLOT);
-    for (int q = threadIdx.x; q < G::SLOT / 4; q += G::NT) row[q] = 0xffffffffu;
+    for (int q = threadIdx.x; q < G::SLOT / 4; q += G::NTC) row[q] = 0xffffffffu;
   }
 }
 
@@ -371,23 +374,24 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
   __shared__ unsigned red[32];
   __shared__ int s_fail;
 
-  // warp 0 starts the copies first; the rest of the block clears the
-  // histograms and fills the rows that hold no frame data meanwhile
-  if (tid < 32) {
-    if (tid == 0) {
-      s_fail = 0;
-      for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    p1_issue_rows<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar, tid);
+  if (tid == G::NTC) {
+    s_fail = 0;
+    for (int c = 0; c < G::NCH; ++c) mbar_init(mbar + c, G::CH);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < G::NHIST * 256; i += G::NT) whist[i] = 0u;
-  p1_fill_rows<R>(jb, ya, nrows_need, xa >= xb, smem);
-  __syncthreads();  // barriers initialised, +inf fills and cleared histograms visible
+  __syncthreads();  // chunk barriers initialised
+  if (tid >= G::NTC) {
+    // producer warp: the row copies, then on to the block's later barriers
+    p1_issue_rows<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar, tid - G::NTC);
+  } else {
+    // compute warps: clear the histograms, fill the rows without frame data
+    for (int i = tid; i < G::NHIST * 256; i += G::NTC) whist[i] = 0u;
+    p1_fill_rows<R>(jb, ya, nrows_need, xa >= xb, smem);
+    asm volatile("bar.sync 1, %0;" ::"r"(G::NTC) : "memory");  // compute warps only
+  }
 
   // ---- phase 1: vertical minima, in place, as the chunks land -----------
-  {
+  if (tid < G::NTC) {
     uint32_t hE[P], hO[P];
     const int j = min(tid, G::NWC - 1);
     const bool owner = tid < G::NWC;
