@@ -38,6 +38,11 @@ Readings of points the paper leaves open (each is a parameter here):
       A_0 = Ahat_0; lam = 0 disables it.
 * C10 quantisation: out = rint(255 * x), half to even.
 * C11 order: gamma, then balance, then quantise; no resize.
+* C13 adaptive gamma ("gamma-adaptive reconstruction" is named in the
+      abstract and Section IV-E without a rule): gamma = ln(mu) / ln(0.5),
+      mu the mean BT.601 luminance of the clipped radiance J, so that
+      mu^(1/gamma) = 0.5; clamped to [0.5, 2.5] (mu <= 0 gives 2.5, mu >= 1
+      gives 0.5). Off by default (fixed gamma, C5).
 * C12 inside the ratio I^c / A^c a channel of A below 1e-6 is floored at
       1e-6 (only reachable when the selected pixels are black in a channel).
 
@@ -67,6 +72,7 @@ class OracleParams:
     top_fraction: float = 0.001    # K as a fraction of N (Section IV-B)
     alpha: float = 0.8             # Eq. 3
     gamma: float = 1.2             # Eq. 8 (value not given by the paper)
+    adaptive_gamma: bool = False   # reading C13
     t_mode: str = "dcp"            # 'dcp' or 'fast' (reading C1)
     color_balance: bool = False
     airlight_ema: float = 0.0      # reading C9
@@ -257,6 +263,24 @@ def recover(I: np.ndarray, t: np.ndarray, A) -> np.ndarray:
     return np.clip(J, 0.0, 1.0)
 
 
+LUMA = (0.299, 0.587, 0.114)       # BT.601 luminance weights (readings C8, C13)
+GAMMA_RANGE = (0.5, 2.5)           # clamp of the adaptive gamma (reading C13)
+
+
+def adaptive_gamma(J: np.ndarray) -> tuple[float, float]:
+    """Reading C13: (gamma, mu) with mu = mean over pixels of the BT.601
+    luminance of J (already clipped to [0, 1]) and gamma = ln(mu) / ln(0.5)
+    clamped to GAMMA_RANGE, so that mu maps to 0.5 under Eq. 8."""
+    Y = LUMA[0] * J[..., 0] + LUMA[1] * J[..., 1] + LUMA[2] * J[..., 2]
+    mu = float(Y.mean())
+    if mu <= 0.0:
+        return GAMMA_RANGE[1], mu
+    if mu >= 1.0:
+        return GAMMA_RANGE[0], mu
+    g = np.log(mu) / np.log(0.5)
+    return float(min(max(g, GAMMA_RANGE[0]), GAMMA_RANGE[1])), mu
+
+
 def gamma_correct(J: np.ndarray, gamma: float) -> np.ndarray:
     """Eq. 8 on normalised J: J_gamma = J^(1/gamma)."""
     return np.power(J, 1.0 / gamma)
@@ -326,7 +350,12 @@ def dehaze_frame(I: np.ndarray, prm: OracleParams, A_prev=None, guided: bool = F
         q = guided_filter(gray(I), t, prm.gf_radius, prm.gf_eps)
         t = np.clip(q, prm.t0, 1.0)
     J = recover(I, t, A)
-    Jg = gamma_correct(J, prm.gamma)
+    extra = {}
+    gamma = prm.gamma
+    if prm.adaptive_gamma:
+        gamma, mu_y = adaptive_gamma(J)
+        extra = {"gamma": gamma, "mean_luma": mu_y}
+    Jg = gamma_correct(J, gamma)
     if prm.color_balance:
         y, gains, mu = gray_world(Jg)
     else:
@@ -334,7 +363,7 @@ def dehaze_frame(I: np.ndarray, prm: OracleParams, A_prev=None, guided: bool = F
     return FrameResult(D=D, K=al["K"], T=al["T"], n_above=al["n_above"],
                        cut_index=al["cut_index"], S=al["S"], A_hat=A_hat, A=A,
                        t=t, J=J, Jg=Jg, gains=gains, mu=mu, out=quantize(y),
-                       t_coarse=t_coarse)
+                       t_coarse=t_coarse, extra=extra)
 
 
 def dehaze_image(I: np.ndarray, prm: OracleParams) -> FrameResult:

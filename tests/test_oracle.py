@@ -375,3 +375,64 @@ def test_transmission_black_airlight_channel_is_finite():
     t = O.transmission_dcp(I, [0.5, 0.0, 0.4], 0.95, 0.1, 3)
     assert np.all(np.isfinite(t))
     np.testing.assert_allclose(t, 1 - 0.95 * (20 / 255) / 0.4, rtol=1e-15)
+
+
+# ---- adaptive gamma (reading C13) -------------------------------------------
+
+def _uniform_frame(rgb, W=23, H=17):
+    I = np.empty((H, W, 3), np.uint8)
+    I[:] = rgb
+    return I
+
+
+@pytest.mark.parametrize("v8", [77, 153])  # v = 0.302, 0.600: inside the unclamped range
+def test_adaptive_gamma_maps_uniform_grey_to_half(v8):
+    """With I = A (override) Eq. 7 gives J = A for every t; a grey A = (v, v, v)
+    has luminance v, and the adaptive exponent sends that mean to 0.5, so the
+    whole frame becomes rint(127.5) = 128 (half to even)."""
+    I = _uniform_frame((v8, v8, v8))
+    v = v8 / 255
+    prm = O.OracleParams(adaptive_gamma=True, airlight_override=(v, v, v), patch=5)
+    r = O.dehaze_frame(I, prm)
+    assert np.all(r.out == 128)
+    assert abs(r.extra["mean_luma"] - v) < 1e-12
+    assert abs(v ** (1.0 / r.extra["gamma"]) - 0.5) < 1e-12
+
+
+@pytest.mark.parametrize("v8,gamma", [(20, 2.5), (26, 2.5), (230, 0.5), (250, 0.5)])
+def test_adaptive_gamma_clamps(v8, gamma):
+    """Means below 0.5^2.5 or above 0.5^0.5 hit the clamp: out = rint(255 v^(1/g))."""
+    I = _uniform_frame((v8, v8, v8))
+    v = v8 / 255
+    r = O.dehaze_frame(I, O.OracleParams(adaptive_gamma=True, airlight_override=(v, v, v), patch=3))
+    assert r.extra["gamma"] == gamma
+    expect = int(np.rint(255 * v ** (1 / gamma)))
+    assert np.all(r.out == expect)
+
+
+def test_adaptive_gamma_black_and_white_frames():
+    """mu = 0 takes the upper clamp (and 0 stays 0); mu = 1 the lower (1 stays 1)."""
+    lo = O.adaptive_gamma(np.zeros((4, 5, 3)))
+    hi = O.adaptive_gamma(np.ones((4, 5, 3)))
+    assert lo == (2.5, 0.0)
+    assert hi[0] == 0.5 and abs(hi[1] - 1.0) < 1e-15
+
+
+def test_adaptive_gamma_green_only_frame_uses_bt601_weight():
+    """BT.601 gives green the weight 0.587: a frame J = (0, g, 0) with
+    0.587 g = 0.25 has mean luminance 0.25 = 0.5^2, hence gamma = 2 and the
+    green channel becomes sqrt(g)."""
+    g = 0.25 / 0.587
+    J = np.zeros((6, 7, 3))
+    J[..., 1] = g
+    gamma, mu = O.adaptive_gamma(J)
+    assert abs(mu - 0.25) < 1e-15 and abs(gamma - 2.0) < 1e-12
+
+
+def test_adaptive_gamma_equals_fixed_gamma_at_its_value():
+    """The adaptive run is the fixed-gamma run at the exponent it chose."""
+    I = hazegen.make_frame(41, 29, seed=12, beta=1.2)
+    a = O.dehaze_frame(I, O.OracleParams(adaptive_gamma=True, patch=7))
+    f = O.dehaze_frame(I, O.OracleParams(gamma=a.extra["gamma"], patch=7))
+    np.testing.assert_array_equal(a.out, f.out)
+    assert 0.5 <= a.extra["gamma"] <= 2.5
