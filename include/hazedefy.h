@@ -92,6 +92,13 @@ typedef struct hz_params {
   int32_t precision;      /* HZ_PREC_FP32 or HZ_PREC_FP16 */
   int32_t use_airlight_override; /* 0/1: use airlight_override as A */
   float airlight_override[3];    /* each in (0, 1] when used */
+  int32_t adaptive_gamma; /* 0/1: per-frame gamma instead of `gamma`: the
+                             exponent that maps the mean BT.601 luminance mu
+                             of the clipped J (Eq. 7) to 0.5 under Eq. 8,
+                             gamma = ln(mu) / ln(0.5), clamped to [0.5, 2.5]
+                             (the paper names gamma-adaptive reconstruction
+                             in Section IV-E without a rule); costs one more
+                             pass over I and P per frame */
 } hz_params;
 
 /* Per-frame results. S, K, T, n_above and cut_index define the selected
@@ -108,6 +115,8 @@ typedef struct hz_frame_info {
   int32_t status;      /* hz_status of this frame */
   float gains[3];      /* colour-balance gains (1 when balance is off) */
   float mean_jg[3];    /* channel means of J_gamma (0 when balance is off) */
+  float gamma;         /* exponent of Eq. 8 used for this frame */
+  float mean_luma;     /* mean BT.601 luminance of J (adaptive gamma; else 0) */
 } hz_frame_info;
 
 /* One frame of a mixed-size batch (hz_dehaze_batch). */

@@ -39,6 +39,7 @@ class hz_params(C.Structure):
         ("precision", C.c_int32),
         ("use_airlight_override", C.c_int32),
         ("airlight_override", C.c_float * 3),
+        ("adaptive_gamma", C.c_int32),
     ]
 
 
@@ -54,6 +55,8 @@ class hz_frame_info(C.Structure):
         ("status", C.c_int32),
         ("gains", C.c_float * 3),
         ("mean_jg", C.c_float * 3),
+        ("gamma", C.c_float),
+        ("mean_luma", C.c_float),
     ]
 
     def as_dict(self):
@@ -61,6 +64,7 @@ class hz_frame_info(C.Structure):
             "A": list(self.A), "A_hat": list(self.A_hat), "K": self.K, "n_above": self.n_above,
             "cut_index": self.cut_index, "S": list(self.S), "T": self.T, "status": self.status,
             "gains": list(self.gains), "mean_jg": list(self.mean_jg),
+            "gamma": self.gamma, "mean_luma": self.mean_luma,
         }
 
 

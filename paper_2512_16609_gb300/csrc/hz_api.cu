@@ -19,6 +19,7 @@ HzKParams kparams_of(const hz_params& p) {
   for (int c = 0; c < 3; ++c) k.ov[c] = p.airlight_override[c];
   k.use_override = p.use_airlight_override;
   k.t_fast = (p.t_mode == HZ_T_FAST) ? 1 : 0;
+  k.adaptive_gamma = p.adaptive_gamma;
   return k;
 }
 
@@ -169,6 +170,14 @@ static hz_status run_front(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, cudaSt
 static hz_status run_recon(hz_ctx* c, HzJobs& jobs, bool balance, cudaStream_t s) {
   const HzKParams kp = kparams_of(c->prm);
   const dim3 g3(max_units(jobs), jobs.n);
+  if (kp.adaptive_gamma) {
+    // per-frame gamma from the mean luminance of J, before the passes that use it
+    {
+      LaunchScope ls(c, HZ_K_BALANCE, s);
+      k_p3<M_LUM_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
+    }
+    HZ_CK(c, cudaGetLastError());
+  }
   if (balance) {
     {
       LaunchScope ls(c, HZ_K_BALANCE, s);
@@ -290,6 +299,8 @@ void recs_to_infos(const HzFrameRec* recs, const LaunchPlan& lp, int n, hz_frame
       o.gains[k] = balance ? r.gains[k] : 1.f;
       o.mean_jg[k] = balance ? r.mean_jg[k] : 0.f;
     }
+    o.gamma = r.gamma_inv > 0.f ? 1.f / r.gamma_inv : 0.f;
+    o.mean_luma = float(r.mean_luma);
     o.K = lp.fp[i].K;
     o.n_above = r.n_above;
     o.cut_index = r.cut_index;
@@ -344,6 +355,7 @@ static hz_status validate(hz_ctx* c, const hz_params* p) {
   if (!(p->gf_eps >= 0.f) || !std::isfinite(p->gf_eps)) return fail(c, HZ_EINVAL, "gf_eps must be >= 0");
   if (p->precision != HZ_PREC_FP32 && p->precision != HZ_PREC_FP16) return fail(c, HZ_EINVAL, "precision");
   if (p->use_airlight_override != 0 && p->use_airlight_override != 1) return fail(c, HZ_EINVAL, "use_airlight_override");
+  if (p->adaptive_gamma != 0 && p->adaptive_gamma != 1) return fail(c, HZ_EINVAL, "adaptive_gamma must be 0 or 1");
   if (p->use_airlight_override)
     for (int k = 0; k < 3; ++k)
       if (!(p->airlight_override[k] > 0.f) || !(p->airlight_override[k] <= 1.f))
@@ -1364,6 +1376,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
       default: break;
     }
     k_p2<<<dim3(P2_BLOCKS, 1), 256, 0, s>>>(jobs, kp);
+    if (kp.adaptive_gamma) k_p3<M_LUM_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
     if (bal) {
       k_p3<M_BAL_SUMS><<<g3, P3_THREADS, 0, s>>>(jobs, kp);
       k_p3<M_BAL_APPLY><<<g3, P3_THREADS, 0, s>>>(jobs, kp);

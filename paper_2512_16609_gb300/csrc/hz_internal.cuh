@@ -51,7 +51,7 @@ constexpr int HZ_STATUS_DEVICE_TIMEOUT = -6;   // per-frame status: a bounded de
 // Per-frame record, zeroed before each launch that uses it.
 struct __align__(16) HzFrameRec {
   unsigned hist[256];           // histogram of D
-  unsigned done_pad, done_p2, done_p3, launch_done;  // launch_done: first record only
+  unsigned done_lum, done_p2, done_p3, launch_done;  // launch_done: first record only
   int T;                        // threshold level
   int status;
   long long n_above;            // #(D > T)
@@ -66,7 +66,9 @@ struct __align__(16) HzFrameRec {
   float inv_fast;               // 1 / (255 * max_c A^c)
   float gains[3];
   float mean_jg[3];
-  float pad2;
+  float gamma_inv;              // 1/gamma of Eq. 8 for this frame
+  double mean_luma;             // mean BT.601 luminance of J (adaptive gamma)
+  double pad3;
 };
 static_assert(sizeof(HzFrameRec) % 16 == 0, "records are packed in arrays");
 
@@ -82,7 +84,7 @@ static_assert(sizeof(HzStreamState) == 48, "stream state is 48 bytes");
 // Where the reconstruction kernel takes t from.
 enum TSource : int { TS_P = 0, TS_FAST = 1, TS_PLANE32 = 2, TS_PLANE16 = 3 };
 // What the reconstruction kernel produces.
-enum P3Mode : int { M_OUT = 0, M_BAL_SUMS = 1, M_BAL_APPLY = 2, M_T_ONLY = 3 };
+enum P3Mode : int { M_OUT = 0, M_BAL_SUMS = 1, M_BAL_APPLY = 2, M_T_ONLY = 3, M_LUM_SUMS = 4 };
 
 // One frame of a launch (read-only for the kernels).
 struct HzJob {
@@ -125,6 +127,7 @@ struct HzKParams {
   int use_override;
   int gamma_is_one;
   int t_fast;
+  int adaptive_gamma;
 };
 
 // ---- small device helpers ----------------------------------------------

@@ -712,6 +712,7 @@ __device__ void fin_frames(const HzJobs& jobs, const HzKParams& kp) {
       amax = fmax(amax, af);
     }
     rec->inv_fast = float(1.0 / (255.0 * amax));
+    rec->gamma_inv = kp.gamma_inv;  // replaced per frame when gamma is adaptive
   }
 }
 
@@ -780,35 +781,6 @@ __global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJ
   fin_frames(jobs, kp);
 }
 
-// Airlight of one frame (thread 0): override, or smoothing through the
-// frame's stream state, and the 1/A factors of the reconstruction.
-__device__ void fin_one(const HzJob& jb, const HzKParams& kp) {
-  HzFrameRec* rec = jb.rec;
-  double A[3];
-  const double Ah[3] = {__ldcg(&rec->A_hat[0]), __ldcg(&rec->A_hat[1]), __ldcg(&rec->A_hat[2])};
-  if (jb.use_override) {
-    for (int c = 0; c < 3; ++c) A[c] = double(kp.ov[c]);
-  } else if (jb.state) {
-    const long long nf = __ldcg(&jb.state->frames);
-    const double lam = double(kp.ema);
-    for (int c = 0; c < 3; ++c)
-      A[c] = (kp.ema > 0.f && nf > 0) ? lam * __ldcg(&jb.state->A[c]) + (1.0 - lam) * Ah[c] : Ah[c];
-    for (int c = 0; c < 3; ++c) jb.state->A[c] = A[c];
-    jb.state->frames = nf + 1;
-  } else {
-    for (int c = 0; c < 3; ++c) A[c] = Ah[c];
-  }
-  double amax = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    rec->A_used[c] = A[c];
-    rec->A[c] = float(A[c]);
-    const double af = fmax(double(float(A[c])), double(A_FLOOR));
-    rec->inv[c] = float(1.0 / (255.0 * af));
-    amax = fmax(amax, af);
-  }
-  rec->inv_fast = float(1.0 / (255.0 * amax));
-}
-
 // ------------------------------------------------------------------------
 // p3: pointwise reconstruction, 16 pixels per thread.
 //
@@ -840,6 +812,8 @@ __device__ __forceinline__ float rcpa(float x) {
 constexpr float TWO23 = 8388608.f;
 constexpr float MAGIC_RINT = 12582912.f;  // 1.5 * 2^23
 constexpr float INV255 = 1.f / 255.f;
+constexpr float LUMA_R = 0.299f, LUMA_G = 0.587f, LUMA_B = 0.114f;  // BT.601 luminance
+constexpr double GAMMA_MIN = 0.5, GAMMA_MAX = 2.5;                   // adaptive gamma clamp
 
 __device__ __forceinline__ uint32_t pack4(float a, float b, float c, float d) {
   const uint32_t lo = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x0040u);
@@ -852,7 +826,7 @@ __device__ __forceinline__ unsigned byte_of(const uint32_t* w, int i) {
 }
 
 struct P3Const {
-  float A[3], inv[3], ninv[3], inv_fast, ninv_fast, gains[3];
+  float A[3], inv[3], ninv[3], inv_fast, ninv_fast, gains[3], gamma_inv;
 };
 
 // t of pixel k of a group (bytes of I in iw, of P in pw; plane pointer tp)
@@ -877,12 +851,17 @@ __device__ __forceinline__ float t_of(const uint32_t* iw, const uint32_t* pw, co
   }
 }
 
+// radiance of one channel (Eq. 7, clipped to [0, 1])
+__device__ __forceinline__ float j_of(float vbits, int c, float rt, const P3Const& K) {
+  const float In = fmaf(vbits, INV255, -TWO23 * INV255);
+  return __saturatef(fmaf(In - K.A[c], rt, K.A[c]));
+}
+
 // gamma-corrected (and, for M_BAL_APPLY, balanced) value of one channel
 template <int MODE>
 __device__ __forceinline__ float jg_of(float vbits, int c, float rt, const P3Const& K, const HzKParams& kp) {
-  const float In = fmaf(vbits, INV255, -TWO23 * INV255);
-  const float J = __saturatef(fmaf(In - K.A[c], rt, K.A[c]));
-  float Jg = kp.gamma_is_one ? J : ex2a(kp.gamma_inv * lg2a(J));
+  const float J = j_of(vbits, c, rt, K);
+  float Jg = (kp.gamma_is_one && !kp.adaptive_gamma) ? J : ex2a(K.gamma_inv * lg2a(J));
   if constexpr (MODE == M_BAL_APPLY) Jg = fminf(Jg * K.gains[c], 1.f);
   return Jg;
 }
@@ -910,19 +889,28 @@ __device__ __forceinline__ void p3_pixels(const HzJob& jb, const HzKParams& kp, 
     for (int k = 0; k < P3_GPX; ++k) {
       const float t = (FULL || k < nv) ? t_of<TS>(iw, pw, tp, k, K, kp) : 1.f;
       const float rt = rcpa(t);
+      if constexpr (MODE == M_LUM_SUMS) {
+        // BT.601 luminance of the clipped radiance (adaptive gamma)
+        const int b = 3 * k;
+        const float y = fmaf(LUMA_R, j_of(bytef(iw[b >> 2], b & 3), 0, rt, K),
+                             fmaf(LUMA_G, j_of(bytef(iw[(b + 1) >> 2], (b + 1) & 3), 1, rt, K),
+                                  LUMA_B * j_of(bytef(iw[(b + 2) >> 2], (b + 2) & 3), 2, rt, K)));
+        if (FULL || k < nv) js0 += y;
+      } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int b = 3 * k + c;
-        const float Jg = jg_of<MODE>(bytef(iw[b >> 2], b & 3), c, rt, K, kp);
-        if constexpr (MODE == M_BAL_SUMS) {
-          if (FULL || k < nv) {
-            if (c == 0) js0 += Jg;
-            else if (c == 1) js1 += Jg;
-            else js2 += Jg;
+        for (int c = 0; c < 3; ++c) {
+          const int b = 3 * k + c;
+          const float Jg = jg_of<MODE>(bytef(iw[b >> 2], b & 3), c, rt, K, kp);
+          if constexpr (MODE == M_BAL_SUMS) {
+            if (FULL || k < nv) {
+              if (c == 0) js0 += Jg;
+              else if (c == 1) js1 += Jg;
+              else js2 += Jg;
+            }
+          } else {
+            q[b & 3] = fmaf(Jg, 255.f, MAGIC_RINT);
+            if ((b & 3) == 3) ow[b >> 2] = pack4(q[0], q[1], q[2], q[3]);
           }
-        } else {
-          q[b & 3] = fmaf(Jg, 255.f, MAGIC_RINT);
-          if ((b & 3) == 3) ow[b >> 2] = pack4(q[0], q[1], q[2], q[3]);
         }
       }
     }
@@ -963,6 +951,7 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
   }
   K.inv_fast = rec->inv_fast;
   K.ninv_fast = -TWO23 * K.inv_fast;
+  K.gamma_inv = kp.adaptive_gamma ? rec->gamma_inv : kp.gamma_inv;
   float js0 = 0.f, js1 = 0.f, js2 = 0.f;
   if (tid < P3_THREADS && g < ngroups) {
     const unsigned yu = g / gpr;
@@ -1014,6 +1003,33 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
         case TS_PLANE32: p3_pixels<MODE, TS_PLANE32, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
         default: p3_pixels<MODE, TS_PLANE16, false>(jb, kp, K, x, y, nv, iw, pw, tp, js0, js1, js2); break;
       }
+    }
+  }
+  if constexpr (MODE == M_LUM_SUMS) {
+    // adaptive gamma: mean luminance of the frame (fixed-order FP64 sum of
+    // per-block sums), gamma = ln(mu) / ln(0.5) clamped to [0.5, 2.5]
+    __shared__ double shd[32];
+    __shared__ int s_last;
+    HzFrameRec* wrec = jb.rec;
+    const double d0 = block_sum((double)js0, shd);
+    if (tid == 0) {
+      jb.bal_part[3 * unit] = d0;
+      __threadfence();
+      s_last = (atomicAdd(&wrec->done_lum, 1u) == unsigned(nunits) - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double a0 = 0.0;
+    for (int u = tid; u < nunits; u += P3_THREADS) a0 += __ldcg(&jb.bal_part[3 * u]);
+    const double t0 = block_sum(a0, shd);
+    if (tid == 0) {
+      const double mu = t0 / (double(jb.W) * double(jb.H));
+      double g = GAMMA_MAX;
+      if (mu >= 1.0) g = GAMMA_MIN;
+      else if (mu > 0.0) g = fmin(fmax(log(mu) / log(0.5), GAMMA_MIN), GAMMA_MAX);
+      wrec->gamma_inv = float(1.0 / g);
+      wrec->mean_luma = mu;
     }
   }
   if constexpr (MODE == M_BAL_SUMS) {

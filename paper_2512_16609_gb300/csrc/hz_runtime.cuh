@@ -184,7 +184,7 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     f.off_tilemax = o;
     o = align_up(o + size_t(f.tiles_x) * f.tiles_y, 256);
     f.off_bal = 0;
-    if (balance) {
+    if (balance || prm.adaptive_gamma) {  // per-unit partial sums of the reductions
       f.off_bal = o;
       o = align_up(o + sizeof(double) * 3 * size_t(f.segs), 256);
     }

@@ -325,3 +325,66 @@ def test_wave_pipeline_matches_one_wave(kw):
         assert res[1][1][f][1] == ref[f].T and res[1][1][f][2] == ref[f].cut_index
         mx, exact = u8_diff(res[1][0][f], ref[f].out)
         assert mx <= 1 and exact > 0.99
+
+
+@pytest.mark.parametrize("kw", [dict(adaptive_gamma=1), dict(adaptive_gamma=1, color_balance=1),
+                                dict(adaptive_gamma=1, t_mode=1, omega=0.5, t0=0.05)])
+@pytest.mark.parametrize("W,H,seed", [(320, 240, 31), (641, 359, 32)])
+def test_adaptive_gamma_matches_oracle(kw, W, H, seed):
+    """Per-frame gamma from the mean luminance of J (reading C13): the
+    exponent within 1e-5 relative of the oracle's, output within 1 LSB."""
+    I = hazegen.make_frame(W, H, seed=seed, beta=1.3)
+    with context(**kw) as (m, ctx):
+        It = to_dev(I, 3)
+        out, _ = empty_dev(W, H)
+        info = m.hz_dehaze_frame(ctx, It, out, want_info=True)
+        o = out.cpu().numpy()
+    ref = O.dehaze_frame(I, oracle_params(**kw))
+    assert abs(info.gamma - ref.extra["gamma"]) <= 1e-5 * ref.extra["gamma"]
+    assert abs(info.mean_luma - ref.extra["mean_luma"]) <= 1e-6
+    mx, exact = u8_diff(o, ref.out)
+    assert mx <= 1 and exact > 0.99
+
+
+def test_adaptive_gamma_uniform_grey_gives_128_and_fixed_gamma_reported():
+    v8 = 77
+    I = np.full((50, 70, 3), v8, np.uint8)
+    v = v8 / 255
+    with context(adaptive_gamma=1, airlight_override=(v, v, v)) as (m, ctx):
+        It = to_dev(I)
+        out, _ = empty_dev(70, 50)
+        info = m.hz_dehaze_frame(ctx, It, out, want_info=True)
+        assert np.all(out.cpu().numpy() == 128)
+        assert abs(info.gamma - np.log(v) / np.log(0.5)) < 1e-5
+    with context(gamma=1.2) as (m, ctx):
+        It = to_dev(hazegen.make_frame(64, 48, seed=2))
+        out, _ = empty_dev(64, 48)
+        info = m.hz_dehaze_frame(ctx, It, out, want_info=True)
+        assert abs(info.gamma - 1.2) < 1e-6 and info.mean_luma == 0.0
+
+
+def test_adaptive_gamma_sequence_and_image_mode():
+    W, H, F = 256, 160, 5
+    frames = hazegen.make_sequence(W, H, F, seed=13, period=F)
+    kw = dict(adaptive_gamma=1, airlight_ema=0.9)
+    with context(**kw) as (m, ctx):
+        m.hz_set_wave_bytes(ctx, 1)  # one frame per wave: the pipelined path
+        inp = torch.from_numpy(frames).cuda()
+        out = torch.empty_like(inp)
+        infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
+        o = out.cpu().numpy()
+    ref = O.dehaze_sequence(list(frames), oracle_params(**kw))
+    for f in range(F):
+        assert abs(infos[f].gamma - ref[f].extra["gamma"]) <= 1e-5 * ref[f].extra["gamma"]
+        mx, exact = u8_diff(o[f], ref[f].out)
+        assert mx <= 1 and exact > 0.99
+    I = frames[0]
+    kw = dict(adaptive_gamma=1, gf_radius=8)
+    with context(**kw) as (m, ctx):
+        out, _ = empty_dev(W, H)
+        info = m.hz_dehaze_image(ctx, to_dev(I), out, want_info=True)
+        o = out.cpu().numpy()
+    ref = O.dehaze_image(I, oracle_params(**kw))
+    assert abs(info.gamma - ref.extra["gamma"]) <= 1e-4 * ref.extra["gamma"]
+    mx, _ = u8_diff(o, ref.out)
+    assert mx <= 1
