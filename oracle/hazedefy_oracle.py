@@ -38,6 +38,11 @@ Readings of points the paper leaves open (each is a parameter here):
       A_0 = Ahat_0; lam = 0 disables it.
 * C10 quantisation: out = rint(255 * x), half to even.
 * C11 order: gamma, then balance, then quantise; no resize.
+* C14 resize to a processing size (Section V, step 1: frames are resized,
+      640x480 by default, before dehazing; no interpolation rule is given):
+      bilinear with half-pixel centres in exact integer arithmetic, weights
+      in units of 1/256 rounded half up, the product rounded half up
+      (resize_bilinear). Off by default (frames at their native size).
 * C13 adaptive gamma ("gamma-adaptive reconstruction" is named in the
       abstract and Section IV-E without a rule): gamma = ln(mu) / ln(0.5),
       mu the mean BT.601 luminance of the clipped radiance J, so that
@@ -73,6 +78,7 @@ class OracleParams:
     alpha: float = 0.8             # Eq. 3
     gamma: float = 1.2             # Eq. 8 (value not given by the paper)
     adaptive_gamma: bool = False   # reading C13
+    proc_size: tuple | None = None # (W, H) processing size (reading C14); None = native
     t_mode: str = "dcp"            # 'dcp' or 'fast' (reading C1)
     color_balance: bool = False
     airlight_ema: float = 0.0      # reading C9
@@ -91,6 +97,45 @@ class OracleParams:
                        top_fraction=r(self.top_fraction), alpha=r(self.alpha),
                        gamma=r(self.gamma), airlight_ema=r(self.airlight_ema),
                        gf_eps=r(self.gf_eps), airlight_override=ov)
+
+
+# ------------------------------------------------------- resize (C14) ----
+
+def _axis_taps(n_in: int, n_out: int):
+    """Per output index: (i0, i1, w1) of the half-pixel-centre bilinear
+    source coordinate u = (i + 1/2) n_in / n_out - 1/2 clamped at 0, in
+    integers: with num = (2i + 1) n_in - n_out and den = 2 n_out,
+    i0 = floor(num / den), w1 = round_half_up(256 (num - i0 den) / den);
+    num < 0 gives (0, 0, 0); i1 = min(i0 + 1, n_in - 1)."""
+    i = np.arange(n_out, dtype=np.int64)
+    num = (2 * i + 1) * n_in - n_out
+    den = 2 * n_out
+    neg = num < 0
+    num = np.where(neg, 0, num)
+    i0 = num // den
+    r = num - i0 * den
+    w1 = (r * 512 + den) // (2 * den)
+    i1 = np.minimum(i0 + 1, n_in - 1)
+    return i0, i1, w1
+
+
+def resize_bilinear(I: np.ndarray, W2: int, H2: int) -> np.ndarray:
+    """Reading C14: bilinear resize with half-pixel centres, exact integers:
+    out = ((256 - wy)((256 - wx) p00 + wx p01) + wy((256 - wx) p10 + wx p11)
+    + 2^15) >> 16 per channel, taps and weights from _axis_taps."""
+    H, W, _ = I.shape
+    x0, x1, wx = _axis_taps(W, W2)
+    y0, y1, wy = _axis_taps(H, H2)
+    P = I.astype(np.int64)
+    p00 = P[y0][:, x0]
+    p01 = P[y0][:, x1]
+    p10 = P[y1][:, x0]
+    p11 = P[y1][:, x1]
+    wx = wx[None, :, None]
+    wy = wy[:, None, None]
+    top = (256 - wx) * p00 + wx * p01
+    bot = (256 - wx) * p10 + wx * p11
+    return (((256 - wy) * top + wy * bot + (1 << 15)) >> 16).astype(np.uint8)
 
 
 # ---------------------------------------------------------------- Eq. 2 ----
@@ -329,6 +374,8 @@ def dehaze_frame(I: np.ndarray, prm: OracleParams, A_prev=None, guided: bool = F
     reconstruction, gamma and optional colour balance, output."""
     if I.ndim != 3 or I.shape[2] != 3 or I.dtype != np.uint8:
         raise ValueError("I must be uint8 (H, W, 3)")
+    if prm.proc_size is not None:
+        I = resize_bilinear(I, prm.proc_size[0], prm.proc_size[1])
     D = dark_channel(I, prm.patch)
     al = airlight(I, D, prm.top_fraction, prm.alpha)
     A_hat = al["A_hat"]

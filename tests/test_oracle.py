@@ -436,3 +436,50 @@ def test_adaptive_gamma_equals_fixed_gamma_at_its_value():
     f = O.dehaze_frame(I, O.OracleParams(gamma=a.extra["gamma"], patch=7))
     np.testing.assert_array_equal(a.out, f.out)
     assert 0.5 <= a.extra["gamma"] <= 2.5
+
+
+# ---- resize to the processing size (reading C14) ----------------------------
+
+def test_resize_identity_and_constant():
+    I = hazegen.random_u8_image(37, 23, 4)
+    np.testing.assert_array_equal(O.resize_bilinear(I, 37, 23), I)
+    C = np.full((31, 45, 3), 173, np.uint8)
+    for (w, h) in [(10, 7), (45, 31), (90, 62), (17, 40)]:
+        assert np.all(O.resize_bilinear(C, w, h) == 173)
+
+
+def test_resize_half_is_rounded_2x2_mean():
+    """Halving puts every output centre midway between 2 x 2 source pixels:
+    the result is their mean, rounded half up."""
+    I = hazegen.random_u8_image(40, 26, 5)
+    out = O.resize_bilinear(I, 20, 13)
+    s = I.astype(np.int64).reshape(13, 2, 20, 2, 3).sum(axis=(1, 3))
+    np.testing.assert_array_equal(out, ((2 * s + 4) // 8).astype(np.uint8))
+
+
+def test_resize_matches_library_bilinear_within_1():
+    """PyTorch's bilinear interpolation (half-pixel centres, no antialias)
+    computes the same interpolant in float, unrounded. Each 1/256 weight is
+    within 1/512 of the exact one and moves the result by at most 255/512
+    per axis, and the final rounding adds 0.5: |out - float| <= 1.5 (and
+    <= 0.5 where no weight is rounded, e.g. an exact 1/3 downscale)."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    for (W, H, W2, H2, seed) in [(64, 48, 40, 30, 1), (50, 30, 123, 77, 2), (1920, 1080, 640, 480, 3),
+                                 (100, 100, 33, 71, 4), (99, 45, 33, 15, 5)]:
+        I = hazegen.random_u8_image(W, H, seed)
+        ref = F.interpolate(torch.from_numpy(I).permute(2, 0, 1)[None].double(), size=(H2, W2),
+                            mode="bilinear", align_corners=False, antialias=False)[0].permute(1, 2, 0).numpy()
+        out = O.resize_bilinear(I, W2, H2).astype(np.float64)
+        bound = 0.5 + 2 * 255 / 512 + 1e-9
+        if W % W2 == 0 and H % H2 == 0 and (W // W2) % 2 == 1 and (H // H2) % 2 == 1:
+            bound = 0.5 + 1e-9  # odd integer factors: centres land on source pixels
+        assert np.abs(out - ref).max() <= bound
+
+
+def test_pipeline_with_processing_size():
+    I = hazegen.make_frame(96, 64, seed=9)
+    r = O.dehaze_frame(I, O.OracleParams(proc_size=(48, 32), patch=7))
+    assert r.out.shape == (32, 48, 3)
+    ref = O.dehaze_frame(O.resize_bilinear(I, 48, 32), O.OracleParams(patch=7))
+    np.testing.assert_array_equal(r.out, ref.out)
