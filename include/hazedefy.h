@@ -99,6 +99,17 @@ typedef struct hz_params {
                              (the paper names gamma-adaptive reconstruction
                              in Section IV-E without a rule); costs one more
                              pass over I and P per frame */
+  int32_t proc_width;     /* processing size (Section V, step 1: each frame is */
+  int32_t proc_height;    /* resized before dehazing, 640x480 by default in the
+                             paper); 0 x 0 = native size. When set, the
+                             dehazing calls (hz_dehaze_frame, _video, _batch,
+                             _image, hz_submit) accept frames of any size and
+                             write outputs of proc_width x proc_height (output
+                             pitch >= 3 * proc_width); the resize is
+                             half-pixel-centre bilinear in exact integers
+                             (1/256 weights, rounded half up). The stage calls
+                             (hz_dark_channel ... hz_recover) never resize.
+                             hz_dehaze_frame_noalloc rejects it. */
 } hz_params;
 
 /* Per-frame results. S, K, T, n_above and cut_index define the selected
@@ -196,6 +207,14 @@ hz_status hz_dehaze_image(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, 
 
 /* D(x) = min_{y in patch(x)} min_c I^c(y) (Eq. 2), window clipped to the
  * image; D is uint8, H rows of W bytes at D_pitch. */
+/* Resize as the dehazing calls do when a processing size is set (Section V,
+ * step 1; half-pixel-centre bilinear in exact integers, 1/256 weights
+ * rounded half up, the weighted sum rounded half up): in (W x H, in_pitch)
+ * -> out (W2 x H2, out_pitch), device pointers, RGB u8 interleaved.
+ * Errors: HZ_EINVAL for bad sizes, pointers or pitches. */
+hz_status hz_resize(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch, uint8_t* out,
+                    int32_t W2, int32_t H2, size_t out_pitch, void* cuda_stream);
+
 hz_status hz_dark_channel(hz_ctx* ctx, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
                           uint8_t* D, size_t D_pitch, void* cuda_stream);
 
@@ -276,7 +295,7 @@ enum {
   HZ_K_BALANCE = 4,   /* colour-balance statistics pass */
   HZ_K_TRANS = 5,     /* transmission plane only (image mode, stage call) */
   HZ_K_GUIDED = 6,    /* guided-filter passes (Eq. 6) */
-  HZ_K_FUSED = 7,     /* persistent fused pipeline */
+  HZ_K_RESIZE = 7,    /* resize to the processing size (Section V, step 1) */
   HZ_K_COUNT = 8
 };
 

@@ -40,6 +40,8 @@ class hz_params(C.Structure):
         ("use_airlight_override", C.c_int32),
         ("airlight_override", C.c_float * 3),
         ("adaptive_gamma", C.c_int32),
+        ("proc_width", C.c_int32),
+        ("proc_height", C.c_int32),
     ]
 
 
@@ -93,7 +95,7 @@ class hz_server_stats(C.Structure):
     ]
 
 
-HZ_K_NAMES = ("dark", "select", "airlight", "recon", "balance", "trans", "guided", "fused")
+HZ_K_NAMES = ("dark", "select", "airlight", "recon", "balance", "trans", "guided", "resize")
 HZ_K_COUNT = 8
 
 
@@ -147,6 +149,7 @@ _SIGS = {
     "hz_reset_server_stats": (C.c_int, [_P]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
     "hz_set_wave_bytes": (C.c_int, [_P, _SZ]),
+    "hz_resize": (C.c_int, [_P, _P, _I, _I, _SZ, _P, _I, _I, _SZ, _P]),
     "hz_autotune_wave_bytes": (C.c_int, [_P, _P, _I, _P, C.POINTER(_SZ), C.POINTER(C.c_float), _I]),
     "hz_set_graph_replay": (C.c_int, [_P, C.c_int]),
     "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
@@ -248,6 +251,14 @@ def hz_get_params(ctx) -> hz_params:
     return p
 
 
+def _check_out(ctx, W, H, out_hw):
+    """Output (H, W) of a dehazing call: the processing size when one is set."""
+    p = hz_get_params(ctx)
+    want = (p.proc_height, p.proc_width) if p.proc_width > 0 else (H, W)
+    if tuple(out_hw) != want:
+        raise ValueError(f"output must be {want[0]}x{want[1]} (H x W), got {out_hw[0]}x{out_hw[1]}")
+
+
 def hz_set_params(ctx, p: hz_params):
     return _check(lib().hz_set_params(ctx, C.byref(p)), ctx, "hz_set_params")
 
@@ -260,8 +271,7 @@ def hz_last_error(ctx) -> str:
 def hz_dehaze_frame(ctx, inp, out, stream_id: int = -1, stream=None, want_info: bool = False):
     pi, W, H, ip = frame_args(inp)
     po, W2, H2, op = frame_args(out)
-    if (W2, H2) != (W, H):
-        raise ValueError("in/out sizes differ")
+    _check_out(ctx, W, H, (H2, W2))
     info = hz_frame_info() if want_info else None
     st = lib().hz_dehaze_frame(ctx, stream_id, pi, W, H, ip, po, op, _stream_ptr(stream),
                                C.byref(info) if info is not None else None)
@@ -273,6 +283,9 @@ def hz_dehaze_video(ctx, inp, out, stream_id: int = -1, flags: int = 0, stream=N
     """inp/out: (F, H, W, 3) uint8 tensors (device, or host when flags has
     HZ_IO_HOST), frames at stride(0)."""
     F, H, W = int(inp.shape[0]), int(inp.shape[1]), int(inp.shape[2])
+    if int(out.shape[0]) != F:
+        raise ValueError("in/out frame counts differ")
+    _check_out(ctx, W, H, (int(out.shape[1]), int(out.shape[2])))
     infos = (hz_frame_info * F)() if want_info else None
     st = lib().hz_dehaze_video(ctx, stream_id, C.c_void_p(inp.data_ptr()), F, W, H, int(inp.stride(1)),
                                int(inp.stride(0)), C.c_void_p(out.data_ptr()), int(out.stride(1)),
@@ -283,6 +296,8 @@ def hz_dehaze_video(ctx, inp, out, stream_id: int = -1, flags: int = 0, stream=N
 
 def hz_dehaze_batch(ctx, frames, outs, stream_ids=None, guided=None, stream=None, want_info: bool = False):
     n = len(frames)
+    for a, b in zip(frames, outs):
+        _check_out(ctx, int(a.shape[1]), int(a.shape[0]), (int(b.shape[0]), int(b.shape[1])))
     descs = _descs(frames, outs, stream_ids, guided)
     infos = (hz_frame_info * max(n, 1))() if want_info else None
     st = lib().hz_dehaze_batch(ctx, descs, n, _stream_ptr(stream), infos)
@@ -290,9 +305,17 @@ def hz_dehaze_batch(ctx, frames, outs, stream_ids=None, guided=None, stream=None
     return infos
 
 
+def hz_resize(ctx, inp, out, stream=None):
+    """Resize inp (H, W, 3) into out (H2, W2, 3) as the processing-size path does."""
+    pi, W, H, ip = frame_args(inp)
+    po, W2, H2, op = frame_args(out)
+    _check(lib().hz_resize(ctx, pi, W, H, ip, po, W2, H2, op, _stream_ptr(stream)), ctx, "hz_resize")
+
+
 def hz_dehaze_image(ctx, inp, out, stream=None, want_info: bool = False):
     pi, W, H, ip = frame_args(inp)
-    po, _, _, op = frame_args(out)
+    po, W2, H2, op = frame_args(out)
+    _check_out(ctx, W, H, (H2, W2))
     info = hz_frame_info() if want_info else None
     st = lib().hz_dehaze_image(ctx, pi, W, H, ip, po, op, _stream_ptr(stream),
                                C.byref(info) if info is not None else None)
@@ -357,7 +380,8 @@ def hz_close_stream(ctx, sid: int):
 def hz_submit(ctx, sid: int, inp, out, flags: int = 0) -> int:
     """inp/out: (H, W, 3) uint8 tensors (host pinned with HZ_IO_HOST, else device)."""
     pi, W, H, ip = frame_args(inp)
-    po, _, _, op = frame_args(out)
+    po, W2, H2, op = frame_args(out)
+    _check_out(ctx, W, H, (H2, W2))
     tk = C.c_uint64(0)
     _check(lib().hz_submit(ctx, sid, pi, ip, po, op, flags, C.byref(tk)), ctx, "hz_submit")
     return tk.value

@@ -139,6 +139,39 @@ cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n,
   return cudaSuccess;
 }
 
+// Inputs of a launch: resized frames go through k_resize into their plan
+// buffers (one launch for all of them), unaligned ones are copied.
+hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base,
+                         cudaStream_t s) {
+  ResizeJobs rj;
+  rj.n = 0;
+  unsigned most = 0;
+  for (int i = 0; i < n; ++i) {
+    const FramePlan& f = lp.fp[i];
+    if (f.resized) {
+      ResizeJob& r = rj.j[rj.n++];
+      r.src = fr[i].in;
+      r.src_pitch = (long long)fr[i].in_pitch;
+      r.dst = base + f.off_copy;
+      r.dst_pitch = f.copy_pitch;
+      r.sW = f.in_W;
+      r.sH = f.in_H;
+      r.dW = f.W;
+      r.dH = f.H;
+      most = std::max(most, unsigned(f.W) * unsigned(f.H));
+    } else if (f.off_copy) {
+      HZ_CK(c, cudaMemcpy2DAsync(base + f.off_copy, size_t(f.copy_pitch), fr[i].in, fr[i].in_pitch,
+                                 size_t(3) * f.W, size_t(f.H), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  if (rj.n) {
+    LaunchScope ls(c, HZ_K_RESIZE, s);
+    k_resize<<<dim3((most + 255) / 256, rj.n), 256, 0, s>>>(rj);
+    HZ_CK(c, cudaGetLastError());
+  }
+  return HZ_OK;
+}
+
 static int max_tiles(const HzJobs& jobs) {
   int m = 1;
   for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].tiles_x * jobs.j[i].tiles_y);
@@ -356,6 +389,10 @@ static hz_status validate(hz_ctx* c, const hz_params* p) {
   if (p->precision != HZ_PREC_FP32 && p->precision != HZ_PREC_FP16) return fail(c, HZ_EINVAL, "precision");
   if (p->use_airlight_override != 0 && p->use_airlight_override != 1) return fail(c, HZ_EINVAL, "use_airlight_override");
   if (p->adaptive_gamma != 0 && p->adaptive_gamma != 1) return fail(c, HZ_EINVAL, "adaptive_gamma must be 0 or 1");
+  if (!(p->proc_width == 0 && p->proc_height == 0) &&
+      (p->proc_width < 1 || p->proc_height < 1 || p->proc_width > HZ_MAX_DIM || p->proc_height > HZ_MAX_DIM ||
+       (long long)p->proc_width * p->proc_height > (1LL << 28)))
+    return fail(c, HZ_EINVAL, "proc_width x proc_height must be 0 x 0 or a valid frame size");
   if (p->use_airlight_override)
     for (int k = 0; k < 3; ++k)
       if (!(p->airlight_override[k] > 0.f) || !(p->airlight_override[k] <= 1.f))
@@ -486,21 +523,30 @@ extern "C" hz_status hz_set_params(hz_ctx* c, const hz_params* p) {
   hz_status st = validate(c, p);
   if (st != HZ_OK) return st;
   std::lock_guard<std::mutex> lk(c->call_mu);
+  if (p->proc_width != c->prm.proc_width || p->proc_height != c->prm.proc_height) {
+    std::lock_guard<std::mutex> sl(c->smu);
+    for (int i = 0; i < MAX_STREAMS; ++i)
+      if (c->stream_open[i]) return fail(c, HZ_ESTATE, "the processing size cannot change while streams are open");
+  }
   c->prm = *p;
   return HZ_OK;
 }
 
 // ------------------------------------------------------------- checks --
 
+// dehaze: the output has the processing size when one is set (stage calls
+// write outputs of the input's size)
 static hz_status check_frame(hz_ctx* c, const void* in, int W, int H, size_t pitch, const void* out,
-                             size_t opitch, bool need_out) {
+                             size_t opitch, bool need_out, bool dehaze = false) {
   if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || (long long)W * H > (1LL << 28))
     return fail(c, HZ_EINVAL, "frame size %dx%d out of range", W, H);
   if (!in) return fail(c, HZ_EINVAL, "input pointer is NULL");
   if (pitch < size_t(3) * W) return fail(c, HZ_EINVAL, "in_pitch %zu < 3*W", pitch);
   if (need_out) {
+    int oW = W, oH = H;
+    if (dehaze) out_dims(c->prm, W, H, oW, oH);
     if (!out) return fail(c, HZ_EINVAL, "output pointer is NULL");
-    if (opitch < size_t(3) * W) return fail(c, HZ_EINVAL, "out_pitch %zu < 3*W", opitch);
+    if (opitch < size_t(3) * oW) return fail(c, HZ_EINVAL, "out_pitch %zu < 3 * output width %d", opitch, oW);
   }
   return HZ_OK;
 }
@@ -538,7 +584,9 @@ static void split_waves(const hz_ctx* c, const hz_frame_desc* fr, int n, std::ve
     size_t bytes = 0;
     int m = 0;
     while (i + m < n && m < MAXJ) {
-      const size_t fb = size_t(3) * fr[i + m].W * fr[i + m].H;
+      int oW, oH;
+      out_dims(c->prm, fr[i + m].W, fr[i + m].H, oW, oH);
+      const size_t fb = size_t(3) * oW * oH;  // the working set is the processed frame
       if (m > 0 && bytes + fb > c->wave_bytes) break;
       bytes += fb;
       ++m;
@@ -554,7 +602,7 @@ static void wave_plan(hz_ctx* c, const hz_frame_desc* fr, int i, int m, bool bal
     Ws[k] = fr[i + k].W;
     Hs[k] = fr[i + k].H;
   }
-  plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp, fr + i);
+  plan_frames(c->prm, Ws.data(), Hs.data(), m, false, bal, lp, fr + i, true);
 }
 
 // Several waves: a three-stage pipeline on the context's streams. The dark
@@ -602,7 +650,7 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
     // stage 1: the slot is free once the reconstruction of wave w - 3 ended
     if (w >= PIPE_SLOTS) HZ_CK(c, cudaStreamWaitEvent(sa, c->ev_free[k], 0));
     HZ_CK(c, cudaMemsetAsync(base, 0, lp.zero_bytes, sa));
-    HZ_CK(c, copy_unaligned(lp, fr + i, m, base, sa));
+    HZ_TRY(prepare_inputs(c, lp, fr + i, m, base, sa));
     HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(max_tiles(jobs), m), sa, jobs));
     HZ_CK(c, cudaEventRecord(c->ev_dark[k], sa));
     // stage 2: selection; its last block runs the airlight chain
@@ -641,7 +689,7 @@ static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStr
   LaunchPlan lp;
   wave_plan(c, fr, 0, n, bal, lp);
   HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
-  HZ_CK(c, copy_unaligned(lp, fr, n, c->arena.base, s));
+  HZ_TRY(prepare_inputs(c, lp, fr, n, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, fr, n, jobs, tsrc);
   if (chain)
@@ -747,7 +795,7 @@ extern "C" hz_status hz_dehaze_frame(hz_ctx* c, int32_t stream_id, const uint8_t
                                      size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
                                      hz_frame_info* info) {
   if (!c) return HZ_EINVAL;
-  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true));
   HZ_TRY(check_stream_id(c, stream_id));
   std::lock_guard<std::mutex> lk(c->call_mu);
   cudaSetDevice(c->device);
@@ -784,9 +832,9 @@ hz_status hz::run_batch(hz_ctx* c, const hz_frame_desc* frames, int n, cudaStrea
   for (int i = 0; i < n; ++i) {
     if (!(frames[i].flags & HZ_GUIDED)) continue;
     LaunchPlan lp;
-    plan_frames(c->prm, &frames[i].W, &frames[i].H, 1, true, bal, lp, frames + i);
+    plan_frames(c->prm, &frames[i].W, &frames[i].H, 1, true, bal, lp, frames + i, true);
     HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
-    HZ_CK(c, copy_unaligned(lp, frames + i, 1, c->arena.base, s));
+    HZ_TRY(prepare_inputs(c, lp, frames + i, 1, c->arena.base, s));
     HzJobs jobs;
     fill_jobs(c, lp, frames + i, 1, jobs, TS_P);
     HZ_TRY(run_image_job(c, lp, jobs, bal, s));
@@ -805,7 +853,7 @@ extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int
   if (n < 0 || (n > 0 && !frames)) return fail(c, HZ_EINVAL, "bad frame list");
   for (int i = 0; i < n; ++i) {
     HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
-                       frames[i].out_pitch, true));
+                       frames[i].out_pitch, true, true));
     HZ_TRY(check_stream_id(c, frames[i].stream_id));
   }
   if (n == 0) return HZ_OK;
@@ -829,11 +877,13 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
                                      void* cuda_stream, hz_frame_info* infos) {
   if (!c) return HZ_EINVAL;
   if (n_frames < 0) return fail(c, HZ_EINVAL, "n_frames < 0");
-  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true));
   HZ_TRY(check_stream_id(c, stream_id));
   if (flags & ~uint32_t(HZ_IO_HOST)) return fail(c, HZ_EINVAL, "unknown flags");
+  int oW, oH;
+  out_dims(c->prm, W, H, oW, oH);
   if (n_frames > 1 && (in_frame_stride < in_pitch * size_t(H - 1) + size_t(3) * W ||
-                       out_frame_stride < out_pitch * size_t(H - 1) + size_t(3) * W))
+                       out_frame_stride < out_pitch * size_t(oH - 1) + size_t(3) * oW))
     return fail(c, HZ_EINVAL, "frame stride smaller than a frame");
   if (n_frames == 0) return HZ_OK;
   std::lock_guard<std::mutex> lk(c->call_mu);
@@ -864,12 +914,12 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
   // pairs; the H2D copy of wave k+1 (copy_in), the compute of wave k (s) and
   // the D2H copy of wave k-1 (copy_out) overlap, so both link directions stay
   // busy. Frames that are contiguous on the host move in one copy per wave.
-  const size_t fin = size_t(3) * W * H, fout = fin;
+  const size_t fin = size_t(3) * W * H, fout = size_t(3) * oW * oH;
   int G = (int)std::max<size_t>(1, HOSTIO_WAVE_BYTES / std::max<size_t>(fin, 1));
   G = std::min(G, MAXJ);
   G = std::min(G, n_frames);
   const bool in_contig = in_pitch == size_t(3) * W && in_frame_stride == fin;
-  const bool out_contig = out_pitch == size_t(3) * W && out_frame_stride == fout;
+  const bool out_contig = out_pitch == size_t(3) * oW && out_frame_stride == fout;
   const size_t half = align_up(size_t(G) * (fin + fout), 4096);
   HZ_TRY(arena_reserve(c, c->stage, HOSTIO_BUFS * half, s));
   HZ_CK(c, cudaEventRecord(c->ev_comp[0], s));
@@ -895,7 +945,7 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
     HZ_CK(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
     std::vector<hz_frame_desc> fr(m);
     for (int k = 0; k < m; ++k)
-      fr[k] = hz_frame_desc{din + size_t(k) * fin, size_t(3) * W, dout + size_t(k) * fout, size_t(3) * W, W, H,
+      fr[k] = hz_frame_desc{din + size_t(k) * fin, size_t(3) * W, dout + size_t(k) * fout, size_t(3) * oW, W, H,
                             stream_id, 0u};
     HZ_TRY(video_device(c, fr.data(), m, s, infos ? infos + f0 : nullptr, chain));
     HZ_CK(c, cudaEventRecord(c->ev_comp[b], s));
@@ -906,7 +956,7 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
     } else {
       for (int k = 0; k < m; ++k)
         HZ_CK(c, cudaMemcpy2DAsync(out + size_t(f0 + k) * out_frame_stride, out_pitch, dout + size_t(k) * fout,
-                                   size_t(3) * W, size_t(3) * W, H, cudaMemcpyDeviceToHost, c->copy_out));
+                                   size_t(3) * oW, size_t(3) * oW, oH, cudaMemcpyDeviceToHost, c->copy_out));
     }
     HZ_CK(c, cudaEventRecord(c->ev_out[b], c->copy_out));
     out_pending[b] = true;
@@ -920,7 +970,7 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
 extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
                                      uint8_t* out, size_t out_pitch, void* cuda_stream, hz_frame_info* info) {
   if (!c) return HZ_EINVAL;
-  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true));
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true));
   std::lock_guard<std::mutex> lk(c->call_mu);
   cudaSetDevice(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -928,9 +978,9 @@ extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, in
   const bool bal = c->prm.color_balance != 0;
   LaunchPlan lp;
   hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, -1, HZ_GUIDED};
-  plan_frames(c->prm, &W, &H, 1, true, bal, lp, &d);
+  plan_frames(c->prm, &W, &H, 1, true, bal, lp, &d, true);
   HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
-  HZ_CK(c, copy_unaligned(lp, &d, 1, c->arena.base, s));
+  HZ_TRY(prepare_inputs(c, lp, &d, 1, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   HZ_TRY(run_image_job(c, lp, jobs, bal, s));
@@ -939,6 +989,26 @@ extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, in
 }
 
 // ---------------------------------------------------------- stage calls --
+
+extern "C" hz_status hz_resize(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch, uint8_t* out,
+                               int32_t W2, int32_t H2, size_t out_pitch, void* cuda_stream) {
+  if (!c) return HZ_EINVAL;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, nullptr, 0, false));
+  HZ_TRY(check_frame(c, out, W2, H2, out_pitch, nullptr, 0, false));
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  cudaSetDevice(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  HZ_TRY(order_after_previous(c, s));
+  ResizeJobs rj;
+  rj.n = 1;
+  rj.j[0] = ResizeJob{in, (long long)in_pitch, out, (long long)out_pitch, W, H, W2, H2};
+  {
+    LaunchScope ls(c, HZ_K_RESIZE, s);
+    k_resize<<<dim3(unsigned((size_t(W2) * H2 + 255) / 256), 1), 256, 0, s>>>(rj);
+  }
+  HZ_CK(c, cudaGetLastError());
+  return mark_done(c, s);
+}
 
 extern "C" hz_status hz_dark_channel(hz_ctx* c, const uint8_t* in, int32_t W, int32_t H, size_t in_pitch,
                                      uint8_t* D, size_t D_pitch, void* cuda_stream) {
@@ -1125,7 +1195,7 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   if (n <= 0 || !frames) return fail(c, HZ_EINVAL, "bad frame list");
   for (int i = 0; i < n; ++i) {
     HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
-                       frames[i].out_pitch, true));
+                       frames[i].out_pitch, true, true));
     HZ_TRY(check_stream_id(c, frames[i].stream_id));
   }
   constexpr int NCAND = int(sizeof TUNE_WAVE_MIB / sizeof TUNE_WAVE_MIB[0]);
@@ -1304,6 +1374,10 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
                                              char* err, size_t err_len) {
   if (validate(nullptr, p) != HZ_OK) {
     noalloc_msg(err, err_len, "invalid parameters");
+    return HZ_EINVAL;
+  }
+  if (p->proc_width != 0) {
+    noalloc_msg(err, err_len, "no processing-size resize in the allocation-free call");
     return HZ_EINVAL;
   }
   if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || !in || !out || in_pitch < size_t(3) * W ||

@@ -75,6 +75,61 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
 }
 
 // ------------------------------------------------------------------------
+// Resize to the processing size (Section V, step 1, which gives no
+// interpolation rule): bilinear with half-pixel centres in exact integers.
+// Along an axis of n_in -> n_out samples, output i samples u = (i + 1/2)
+// n_in / n_out - 1/2 (clamped at 0): with num = (2i + 1) n_in - n_out and
+// den = 2 n_out, i0 = num / den, the weight of i0 + 1 is the remainder
+// scaled to 1/256 and rounded half up, and i0 + 1 is clamped to n_in - 1.
+// out = ((256 - wy)((256 - wx) p00 + wx p01) + wy((256 - wx) p10 + wx p11)
+// + 2^15) >> 16 per channel. Sizes up to HZ_MAX_DIM keep every product
+// inside 32 bits.
+struct ResizeJob {
+  const uint8_t* src;
+  long long src_pitch;
+  uint8_t* dst;
+  long long dst_pitch;
+  int sW, sH, dW, dH;
+};
+struct ResizeJobs {
+  int n;
+  int pad;
+  ResizeJob j[MAXJ];
+};
+
+__device__ __forceinline__ void resize_taps(int i, int n_in, int n_out, int& i0, int& i1, int& w1) {
+  const int num = (2 * i + 1) * n_in - n_out, den = 2 * n_out;
+  if (num < 0) {
+    i0 = 0;
+    w1 = 0;
+  } else {
+    i0 = num / den;
+    const int r = num - i0 * den;
+    w1 = (r * 512 + den) / (2 * den);
+  }
+  i1 = min(i0 + 1, n_in - 1);
+}
+
+__global__ void __launch_bounds__(256) k_resize(const __grid_constant__ ResizeJobs jobs) {
+  const ResizeJob& r = jobs.j[blockIdx.y];
+  const unsigned i = blockIdx.x * 256u + threadIdx.x;
+  if (i >= unsigned(r.dW) * unsigned(r.dH)) return;
+  const int y = int(i / unsigned(r.dW)), x = int(i - unsigned(y) * unsigned(r.dW));
+  int x0, x1, wx, y0, y1, wy;
+  resize_taps(x, r.sW, r.dW, x0, x1, wx);
+  resize_taps(y, r.sH, r.dH, y0, y1, wy);
+  const uint8_t* a = r.src + (long long)y0 * r.src_pitch;
+  const uint8_t* b = r.src + (long long)y1 * r.src_pitch;
+  uint8_t* o = r.dst + (long long)y * r.dst_pitch + 3LL * x;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int top = (256 - wx) * int(__ldg(a + 3 * x0 + c)) + wx * int(__ldg(a + 3 * x1 + c));
+    const int bot = (256 - wx) * int(__ldg(b + 3 * x0 + c)) + wx * int(__ldg(b + 3 * x1 + c));
+    o[c] = uint8_t(((256 - wy) * top + wy * bot + (1 << 15)) >> 16);
+  }
+}
+
+// ------------------------------------------------------------------------
 // p1: one region of one frame: P1_SW output pixels wide (a strip), BH =
 // M (2R + 1) output rows tall (a band).
 //

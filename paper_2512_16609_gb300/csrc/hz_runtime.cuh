@@ -128,8 +128,10 @@ struct FramePlan {
   size_t off_P, off_tilemax, off_bal;      // in the rest
   size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
   long long plane_pitch32, plane_pitch16;
-  size_t off_copy;                          // aligned copy of an unaligned input (0 if none)
-  long long copy_pitch;
+  size_t off_copy;                          // aligned copy of an unaligned input, or the resized
+  long long copy_pitch;                     // frame (0 if none)
+  int in_W = 0, in_H = 0;                   // input size of a resized frame
+  bool resized = false;                     // W x H is the processing size, input is in_W x in_H
 };
 
 struct LaunchPlan {
@@ -153,8 +155,17 @@ inline long long num_top(long long N, float frac) {
 // aligned buffer of the plan.
 inline bool input_aligned16(const void* p, size_t pitch) { return ((uintptr_t(p) | uintptr_t(pitch)) & 15) == 0; }
 
+// Output size of a dehazing call for a W x H input: the processing size when
+// one is set, else the input size.
+inline void out_dims(const hz_params& prm, int W, int H, int& oW, int& oH) {
+  oW = prm.proc_width > 0 ? prm.proc_width : W;
+  oH = prm.proc_width > 0 ? prm.proc_height : H;
+}
+
+// resize: the dehazing paths (frames go to the processing size when one is
+// set); the stage calls plan frames as they are.
 inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int n, bool image, bool balance,
-                        LaunchPlan& lp, const hz_frame_desc* fr = nullptr) {
+                        LaunchPlan& lp, const hz_frame_desc* fr = nullptr, bool resize = false) {
   lp.fp.resize(n);
   // zeroed region: the n records first (contiguous, one copy reads them
   // back), then the per-row tie counts and sums
@@ -163,6 +174,12 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     FramePlan& f = lp.fp[i];
     f.W = Ws[i];
     f.H = Hs[i];
+    f.resized = resize && prm.proc_width > 0;
+    if (f.resized) {
+      f.in_W = Ws[i];
+      f.in_H = Hs[i];
+      out_dims(prm, Ws[i], Hs[i], f.W, f.H);
+    }
     f.band_h = p1_band_rows(prm.patch / 2);
     f.tiles_x = (f.W + P1_SW - 1) / P1_SW;
     f.tiles_y = (f.H + f.band_h - 1) / f.band_h;
@@ -190,7 +207,7 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     }
     f.off_copy = 0;
     f.copy_pitch = 0;
-    if (fr && !input_aligned16(fr[i].in, fr[i].in_pitch)) {
+    if (f.resized || (fr && !input_aligned16(fr[i].in, fr[i].in_pitch))) {
       f.copy_pitch = (long long)align_up(size_t(3) * f.W, 16);
       f.off_copy = o;
       o = align_up(o + size_t(f.copy_pitch) * f.H, 1024);

@@ -89,7 +89,7 @@ static void complete_loop(Server* S) {
         const int i = sl.order[k];
         const Request& r = sl.reqs[i];
         LaunchPlan lp;
-        plan_frames(c->prm, &r.W, &r.H, 1, false, false, lp);
+        plan_frames(c->prm, &r.W, &r.H, 1, false, false, lp, nullptr, true);
         recs_to_infos(sl.recs + k, lp, 1, &infos[i], bal);
       }
     }
@@ -121,7 +121,11 @@ static hz_status launch_batch(Server* S, Slot& sl) {
   const int n = (int)sl.reqs.size();
   size_t need = 0;
   for (const Request& r : sl.reqs)
-    if (r.flags & HZ_IO_HOST) need += 2 * align_up(size_t(3) * r.W * r.H, 256);
+    if (r.flags & HZ_IO_HOST) {
+      int oW, oH;
+      out_dims(c->prm, r.W, r.H, oW, oH);
+      need += align_up(size_t(3) * r.W * r.H, 256) + align_up(size_t(3) * oW * oH, 256);
+    }
   if (need > sl.stage.cap) {
     if (sl.stage.base) cudaFree(sl.stage.base);
     sl.stage.base = nullptr;
@@ -143,16 +147,18 @@ static hz_status launch_batch(Server* S, Slot& sl) {
                           c->stream_flags[r.sid] & HZ_GUIDED};
     if (r.flags & HZ_IO_HOST) {
       any_host = true;
+      int oW, oH;
+      out_dims(c->prm, r.W, r.H, oW, oH);
       const size_t fb = align_up(size_t(3) * r.W * r.H, 256);
       uint8_t* din = sl.stage.base + o;
       uint8_t* dout = din + fb;
-      o += 2 * fb;
+      o += fb + align_up(size_t(3) * oW * oH, 256);
       HZ_CK(c, cudaMemcpy2DAsync(din, size_t(3) * r.W, r.in, r.in_pitch, size_t(3) * r.W, r.H,
                                  cudaMemcpyHostToDevice, S->s_h2d));
       fr[i].in = din;
       fr[i].in_pitch = size_t(3) * r.W;
       fr[i].out = dout;
-      fr[i].out_pitch = size_t(3) * r.W;
+      fr[i].out_pitch = size_t(3) * oW;
     }
   }
   HZ_CK(c, cudaEventRecord(sl.ev_h2d, S->s_h2d));
@@ -170,7 +176,9 @@ static hz_status launch_batch(Server* S, Slot& sl) {
     for (int i = 0; i < n; ++i) {
       const Request& r = sl.reqs[i];
       if (!(r.flags & HZ_IO_HOST)) continue;
-      HZ_CK(c, cudaMemcpy2DAsync(r.out, r.out_pitch, fr[i].out, fr[i].out_pitch, size_t(3) * r.W, r.H,
+      int oW, oH;
+      out_dims(c->prm, r.W, r.H, oW, oH);
+      HZ_CK(c, cudaMemcpy2DAsync(r.out, r.out_pitch, fr[i].out, fr[i].out_pitch, size_t(3) * oW, oH,
                                  cudaMemcpyDeviceToHost, S->s_d2h));
     }
   }
@@ -288,9 +296,11 @@ using namespace hz;
 
 static size_t stream_footprint(const hz_params& prm, int W, int H, unsigned flags) {
   LaunchPlan lp;
-  plan_frames(prm, &W, &H, 1, (flags & HZ_GUIDED) != 0, prm.color_balance != 0, lp);
+  plan_frames(prm, &W, &H, 1, (flags & HZ_GUIDED) != 0, prm.color_balance != 0, lp, nullptr, true);
   // resident scratch of one frame in flight plus in/out staging
-  return lp.total + 2 * align_up(size_t(3) * W * H, 4096);
+  int oW, oH;
+  out_dims(prm, W, H, oW, oH);
+  return lp.total + align_up(size_t(3) * W * H, 4096) + align_up(size_t(3) * oW * oH, 4096);
 }
 
 extern "C" hz_status hz_open_stream(hz_ctx* c, int32_t W, int32_t H, uint32_t flags, int32_t* stream_id) {
@@ -382,7 +392,9 @@ extern "C" hz_status hz_submit(hz_ctx* c, int32_t sid, const uint8_t* in, size_t
     W = c->stream_W[sid];
     H = c->stream_H[sid];
   }
-  if (!in || !out || in_pitch < size_t(3) * W || out_pitch < size_t(3) * W)
+  int oW, oH;
+  out_dims(c->prm, W, H, oW, oH);
+  if (!in || !out || in_pitch < size_t(3) * W || out_pitch < size_t(3) * oW)
     return fail(c, HZ_EINVAL, "bad buffers for a %dx%d stream", W, H);
   {
     std::lock_guard<std::mutex> lk(c->smu);
