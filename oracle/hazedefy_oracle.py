@@ -43,6 +43,12 @@ Readings of points the paper leaves open (each is a parameter here):
       bilinear with half-pixel centres in exact integer arithmetic, weights
       in units of 1/256 rounded half up, the product rounded half up
       (resize_bilinear). Off by default (frames at their native size).
+* C15 camera-native NV12 input (the paper's target is live camera feeds,
+      Section V; decoders and cameras deliver 4:2:0 YCbCr): BT.601
+      limited-range YCbCr to RGB with the common 8-bit integer coefficients
+      (298, 409, 100, 208, 516; +128 and >> 8, clipped to [0, 255]), each
+      chroma sample shared by its 2 x 2 block of pixels (nv12_to_rgb); the
+      conversion precedes the resize of C14.
 * C13 adaptive gamma ("gamma-adaptive reconstruction" is named in the
       abstract and Section IV-E without a rule): gamma = ln(mu) / ln(0.5),
       mu the mean BT.601 luminance of the clipped radiance J, so that
@@ -97,6 +103,26 @@ class OracleParams:
                        top_fraction=r(self.top_fraction), alpha=r(self.alpha),
                        gamma=r(self.gamma), airlight_ema=r(self.airlight_ema),
                        gf_eps=r(self.gf_eps), airlight_override=ov)
+
+
+# -------------------------------------------------- NV12 input (C15) ----
+
+def nv12_to_rgb(Y: np.ndarray, UV: np.ndarray) -> np.ndarray:
+    """Reading C15: Y (H, W) and interleaved chroma UV (H/2, W/2, 2) (Cb, Cr)
+    of an NV12 frame to RGB u8 (H, W, 3): with C = Y - 16, D = Cb - 128,
+    E = Cr - 128, R = (298 C + 409 E + 128) >> 8, G = (298 C - 100 D -
+    208 E + 128) >> 8, B = (298 C + 516 D + 128) >> 8, each clipped to
+    [0, 255]; pixel (x, y) takes the chroma sample (x // 2, y // 2)."""
+    H, W = Y.shape
+    if H % 2 or W % 2 or UV.shape != (H // 2, W // 2, 2):
+        raise ValueError("NV12 needs even W and H and a (H/2, W/2, 2) chroma plane")
+    C = Y.astype(np.int64) - 16
+    U = np.repeat(np.repeat(UV[..., 0].astype(np.int64), 2, axis=0), 2, axis=1) - 128
+    V = np.repeat(np.repeat(UV[..., 1].astype(np.int64), 2, axis=0), 2, axis=1) - 128
+    R = (298 * C + 409 * V + 128) >> 8
+    G = (298 * C - 100 * U - 208 * V + 128) >> 8
+    B = (298 * C + 516 * U + 128) >> 8
+    return np.clip(np.stack([R, G, B], axis=-1), 0, 255).astype(np.uint8)
 
 
 # ------------------------------------------------------- resize (C14) ----

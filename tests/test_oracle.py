@@ -483,3 +483,48 @@ def test_pipeline_with_processing_size():
     assert r.out.shape == (32, 48, 3)
     ref = O.dehaze_frame(O.resize_bilinear(I, 48, 32), O.OracleParams(patch=7))
     np.testing.assert_array_equal(r.out, ref.out)
+
+
+# ---- NV12 input (reading C15) -------------------------------------------------
+
+def test_nv12_black_white_and_grey_ramp():
+    """Limited range: Y 16 is black, 235 white; neutral chroma gives grey
+    levels 255 (Y - 16) / 219 rounded (to within the 8-bit coefficient)."""
+    Y = np.array([[16, 235], [126, 200]], np.uint8)
+    UV = np.full((1, 1, 2), 128, np.uint8)
+    rgb = O.nv12_to_rgb(Y, UV)
+    assert tuple(rgb[0, 0]) == (0, 0, 0) and tuple(rgb[0, 1]) == (255, 255, 255)
+    for y in range(2):
+        for x in range(2):
+            r, g, b = rgb[y, x]
+            assert r == g == b
+            assert abs(int(r) - 255 * (int(Y[y, x]) - 16) / 219) <= 0.6
+
+
+def test_nv12_matches_float_bt601_within_1():
+    """The float BT.601 limited-range matrix (1.164, 1.596, 0.392, 0.813,
+    2.017) agrees with the 8-bit integer form within 1 LSB away from the
+    clipping bounds."""
+    g = np.random.default_rng(3)
+    Y = g.integers(16, 236, size=(32, 48), dtype=np.uint8)
+    UV = g.integers(16, 241, size=(16, 24, 2), dtype=np.uint8)
+    rgb = O.nv12_to_rgb(Y, UV).astype(np.float64)
+    C = Y.astype(np.float64) - 16
+    U = np.repeat(np.repeat(UV[..., 0].astype(np.float64) - 128, 2, 0), 2, 1)
+    V = np.repeat(np.repeat(UV[..., 1].astype(np.float64) - 128, 2, 0), 2, 1)
+    ref = np.stack([1.164 * C + 1.596 * V, 1.164 * C - 0.392 * U - 0.813 * V, 1.164 * C + 2.017 * U], -1)
+    inside = (ref > 1) & (ref < 254)
+    assert np.abs(rgb - ref)[inside].max() <= 1.0
+
+
+def test_nv12_chroma_shared_by_2x2_blocks():
+    Y = np.full((4, 6), 120, np.uint8)
+    UV = np.zeros((2, 3, 2), np.uint8)
+    UV[..., 0] = [[90, 128, 200], [60, 128, 160]]
+    UV[..., 1] = [[200, 128, 90], [100, 150, 128]]
+    rgb = O.nv12_to_rgb(Y, UV)
+    for by in range(2):
+        for bx in range(3):
+            blk = rgb[2 * by:2 * by + 2, 2 * bx:2 * bx + 2].reshape(4, 3)
+            assert (blk == blk[0]).all()
+    assert not (rgb[0, 0] == rgb[0, 2]).all()
