@@ -40,6 +40,7 @@ __all__ = [
     "sequence_beta",
     "mixed_batch_specs",
     "random_u8_image",
+    "rgb_to_nv12",
 ]
 
 BASE_AIRLIGHT = (0.85, 0.88, 0.90)
@@ -179,3 +180,27 @@ def random_u8_image(W: int, H: int, seed: int, levels: int = 256) -> np.ndarray:
     """Unstructured uint8 RGB noise (H, W, 3) with values in [0, levels)."""
     g = _rng(seed)
     return g.integers(0, levels, size=(H, W, 3), dtype=np.uint8)
+
+
+def rgb_to_nv12(I: np.ndarray) -> np.ndarray:
+    """A camera-style NV12 frame (3H/2, W) uint8 from an RGB frame (H, W, 3)
+    with even sizes: BT.601 limited-range forward transform in float
+    (Y = 16 + 65.481 R + 128.553 G + 24.966 B, Cb = 128 - 37.797 R - 74.203 G
+    + 112 B, Cr = 128 + 112 R - 93.786 G - 18.214 B on R, G, B in [0, 1]),
+    chroma averaged over 2 x 2 blocks, rounded and clipped; the luma rows,
+    then the interleaved Cb/Cr rows."""
+    H, W, _ = I.shape
+    if H % 2 or W % 2:
+        raise ValueError("NV12 needs even W and H")
+    x = I.astype(np.float64) / 255.0
+    R, G, B = x[..., 0], x[..., 1], x[..., 2]
+    Y = 16 + 65.481 * R + 128.553 * G + 24.966 * B
+    Cb = 128 - 37.797 * R - 74.203 * G + 112.0 * B
+    Cr = 128 + 112.0 * R - 93.786 * G - 18.214 * B
+    Cb = Cb.reshape(H // 2, 2, W // 2, 2).mean(axis=(1, 3))
+    Cr = Cr.reshape(H // 2, 2, W // 2, 2).mean(axis=(1, 3))
+    out = np.empty((H + H // 2, W), np.uint8)
+    out[:H] = np.clip(np.rint(Y), 0, 255)
+    uv = np.stack([Cb, Cr], axis=-1).reshape(H // 2, W)
+    out[H:] = np.clip(np.rint(uv), 0, 255)
+    return out

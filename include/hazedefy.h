@@ -71,6 +71,15 @@ enum { HZ_MAX_PATCH = 31, HZ_MAX_GF_RADIUS = 255, HZ_MAX_DIM = 16384 };
 /* flags */
 #define HZ_IO_HOST 0x1u  /* in/out are host memory; the library stages copies */
 #define HZ_GUIDED 0x2u   /* hz_open_stream: refine t with the guided filter */
+/* The input is an NV12 frame, as camera pipelines and video decoders deliver
+ * it: the Y plane (W x H bytes, row pitch in_pitch) followed at in + in_pitch
+ * * H by the interleaved Cb/Cr plane (W/2 pairs x H/2 rows, same pitch); W
+ * and H even, in_pitch >= W. It is converted to RGB before the dark channel
+ * (BT.601 limited range, 8-bit integer coefficients 298/409/100/208/516,
+ * each chroma sample shared by its 2 x 2 pixels), then resized when a
+ * processing size is set. Accepted by hz_dehaze_video (flags),
+ * hz_dehaze_batch (hz_frame_desc.flags) and hz_open_stream (flags). */
+#define HZ_INPUT_NV12 0x4u
 
 /* Parameters. Intensities are normalised to [0, 1] (I_n = I / 255); the
  * airlight A is in the same units. Set struct_size = sizeof(hz_params). */

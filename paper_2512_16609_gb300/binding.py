@@ -18,7 +18,7 @@ HZ_ETIMEDOUT, HZ_ECUDA, HZ_EDEVICE_TIMEOUT, HZ_ESTATE = -4, -5, -6, -7
 HZ_T_DCP, HZ_T_FAST = 0, 1
 HZ_PREC_FP32, HZ_PREC_FP16 = 0, 1
 HZ_MAX_PATCH, HZ_MAX_GF_RADIUS, HZ_MAX_DIM = 31, 255, 16384
-HZ_IO_HOST, HZ_GUIDED = 0x1, 0x2
+HZ_IO_HOST, HZ_GUIDED, HZ_INPUT_NV12 = 0x1, 0x2, 0x4
 HZ_STREAM_STATE_BYTES = 48
 
 
@@ -213,6 +213,19 @@ def frame_args(t):
     return C.c_void_p(t.data_ptr()), int(t.shape[1]), int(t.shape[0]), int(t.stride(0))
 
 
+def nv12_args(t):
+    """(pointer, W, H, pitch) of an NV12 frame held as a uint8 (3H/2, W)
+    tensor: H luma rows, then H/2 rows of interleaved Cb/Cr, one pitch."""
+    import torch
+    if t.dtype != torch.uint8 or t.dim() != 2 or t.stride(1) != 1 or t.shape[0] % 3:
+        raise ValueError("NV12 frame must be uint8 (3H/2, W) with unit column stride")
+    return C.c_void_p(t.data_ptr()), int(t.shape[1]), int(t.shape[0]) * 2 // 3, int(t.stride(0))
+
+
+def in_args(t, nv12=False):
+    return nv12_args(t) if nv12 else frame_args(t)
+
+
 def plane_args(t):
     """(pointer, pitch in bytes) of a 2-D float32 tensor with unit column stride."""
     if t.dim() != 2 or t.stride(1) != 1:
@@ -281,8 +294,11 @@ def hz_dehaze_frame(ctx, inp, out, stream_id: int = -1, stream=None, want_info: 
 
 def hz_dehaze_video(ctx, inp, out, stream_id: int = -1, flags: int = 0, stream=None, want_info: bool = False):
     """inp/out: (F, H, W, 3) uint8 tensors (device, or host when flags has
-    HZ_IO_HOST), frames at stride(0)."""
-    F, H, W = int(inp.shape[0]), int(inp.shape[1]), int(inp.shape[2])
+    HZ_IO_HOST), frames at stride(0); with HZ_INPUT_NV12, inp is (F, 3H/2, W)."""
+    if flags & HZ_INPUT_NV12:
+        F, H, W = int(inp.shape[0]), int(inp.shape[1]) * 2 // 3, int(inp.shape[2])
+    else:
+        F, H, W = int(inp.shape[0]), int(inp.shape[1]), int(inp.shape[2])
     if int(out.shape[0]) != F:
         raise ValueError("in/out frame counts differ")
     _check_out(ctx, W, H, (int(out.shape[1]), int(out.shape[2])))
@@ -294,11 +310,14 @@ def hz_dehaze_video(ctx, inp, out, stream_id: int = -1, flags: int = 0, stream=N
     return infos
 
 
-def hz_dehaze_batch(ctx, frames, outs, stream_ids=None, guided=None, stream=None, want_info: bool = False):
+def hz_dehaze_batch(ctx, frames, outs, stream_ids=None, guided=None, stream=None, want_info: bool = False,
+                    nv12=None):
+    """frames: (H, W, 3) RGB tensors, or (3H/2, W) NV12 tensors where nv12[i]."""
     n = len(frames)
-    for a, b in zip(frames, outs):
-        _check_out(ctx, int(a.shape[1]), int(a.shape[0]), (int(b.shape[0]), int(b.shape[1])))
-    descs = _descs(frames, outs, stream_ids, guided)
+    for i, (a, b) in enumerate(zip(frames, outs)):
+        _, W, H, _ = in_args(a, nv12 is not None and nv12[i])
+        _check_out(ctx, W, H, (int(b.shape[0]), int(b.shape[1])))
+    descs = _descs(frames, outs, stream_ids, guided, nv12)
     infos = (hz_frame_info * max(n, 1))() if want_info else None
     st = lib().hz_dehaze_batch(ctx, descs, n, _stream_ptr(stream), infos)
     _check(st, ctx, "hz_dehaze_batch")
@@ -377,9 +396,10 @@ def hz_close_stream(ctx, sid: int):
     return _check(lib().hz_close_stream(ctx, sid), ctx, "hz_close_stream")
 
 
-def hz_submit(ctx, sid: int, inp, out, flags: int = 0) -> int:
-    """inp/out: (H, W, 3) uint8 tensors (host pinned with HZ_IO_HOST, else device)."""
-    pi, W, H, ip = frame_args(inp)
+def hz_submit(ctx, sid: int, inp, out, flags: int = 0, nv12: bool = False) -> int:
+    """inp/out: (H, W, 3) uint8 tensors (host pinned with HZ_IO_HOST, else
+    device); inp is (3H/2, W) for a stream opened with HZ_INPUT_NV12 (nv12=True)."""
+    pi, W, H, ip = in_args(inp, nv12)
     po, W2, H2, op = frame_args(out)
     _check_out(ctx, W, H, (H2, W2))
     tk = C.c_uint64(0)
@@ -442,11 +462,11 @@ def hz_set_wave_bytes(ctx, nbytes: int):
 TUNE_WAVE_MIB = (8, 16, 32, 64, 128, 192, 256)
 
 
-def _descs(frames, outs, stream_ids=None, guided=None):
+def _descs(frames, outs, stream_ids=None, guided=None, nv12=None):
     n = len(frames)
     descs = (hz_frame_desc * max(n, 1))()
     for i, (a, b) in enumerate(zip(frames, outs)):
-        pi, W, H, ip = frame_args(a)
+        pi, W, H, ip = in_args(a, nv12 is not None and nv12[i])
         po, _, _, op = frame_args(b)
         descs[i].in_ = pi.value
         descs[i].in_pitch = ip
@@ -455,7 +475,8 @@ def _descs(frames, outs, stream_ids=None, guided=None):
         descs[i].W = W
         descs[i].H = H
         descs[i].stream_id = -1 if stream_ids is None else int(stream_ids[i])
-        descs[i].flags = HZ_GUIDED if (guided is not None and guided[i]) else 0
+        descs[i].flags = (HZ_GUIDED if (guided is not None and guided[i]) else 0) | \
+            (HZ_INPUT_NV12 if (nv12 is not None and nv12[i]) else 0)
     return descs
 
 

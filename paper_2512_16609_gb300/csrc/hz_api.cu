@@ -148,7 +148,7 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
   unsigned most = 0;
   for (int i = 0; i < n; ++i) {
     const FramePlan& f = lp.fp[i];
-    if (f.resized) {
+    if (f.resized || f.nv12) {
       ResizeJob& r = rj.j[rj.n++];
       r.src = fr[i].in;
       r.src_pitch = (long long)fr[i].in_pitch;
@@ -158,6 +158,8 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
       r.sH = f.in_H;
       r.dW = f.W;
       r.dH = f.H;
+      r.nv12 = f.nv12 ? 1 : 0;
+      r.pad = 0;
       most = std::max(most, unsigned(f.W) * unsigned(f.H));
     } else if (f.off_copy) {
       HZ_CK(c, cudaMemcpy2DAsync(base + f.off_copy, size_t(f.copy_pitch), fr[i].in, fr[i].in_pitch,
@@ -537,11 +539,16 @@ extern "C" hz_status hz_set_params(hz_ctx* c, const hz_params* p) {
 // dehaze: the output has the processing size when one is set (stage calls
 // write outputs of the input's size)
 static hz_status check_frame(hz_ctx* c, const void* in, int W, int H, size_t pitch, const void* out,
-                             size_t opitch, bool need_out, bool dehaze = false) {
+                             size_t opitch, bool need_out, bool dehaze = false, bool nv12 = false) {
   if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || (long long)W * H > (1LL << 28))
     return fail(c, HZ_EINVAL, "frame size %dx%d out of range", W, H);
   if (!in) return fail(c, HZ_EINVAL, "input pointer is NULL");
-  if (pitch < size_t(3) * W) return fail(c, HZ_EINVAL, "in_pitch %zu < 3*W", pitch);
+  if (nv12) {
+    if ((W | H) & 1) return fail(c, HZ_EINVAL, "NV12 frames need even sizes (%dx%d)", W, H);
+    if (pitch < size_t(W)) return fail(c, HZ_EINVAL, "NV12 in_pitch %zu < W", pitch);
+  } else if (pitch < size_t(3) * W) {
+    return fail(c, HZ_EINVAL, "in_pitch %zu < 3*W", pitch);
+  }
   if (need_out) {
     int oW = W, oH = H;
     if (dehaze) out_dims(c->prm, W, H, oW, oH);
@@ -852,8 +859,9 @@ extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int
   if (!c) return HZ_EINVAL;
   if (n < 0 || (n > 0 && !frames)) return fail(c, HZ_EINVAL, "bad frame list");
   for (int i = 0; i < n; ++i) {
+    if (frames[i].flags & ~uint32_t(HZ_GUIDED | HZ_INPUT_NV12)) return fail(c, HZ_EINVAL, "unknown frame flags");
     HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
-                       frames[i].out_pitch, true, true));
+                       frames[i].out_pitch, true, true, (frames[i].flags & HZ_INPUT_NV12) != 0));
     HZ_TRY(check_stream_id(c, frames[i].stream_id));
   }
   if (n == 0) return HZ_OK;
@@ -877,12 +885,16 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
                                      void* cuda_stream, hz_frame_info* infos) {
   if (!c) return HZ_EINVAL;
   if (n_frames < 0) return fail(c, HZ_EINVAL, "n_frames < 0");
-  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true));
+  if (flags & ~uint32_t(HZ_IO_HOST | HZ_INPUT_NV12)) return fail(c, HZ_EINVAL, "unknown flags");
+  const bool nv12 = (flags & HZ_INPUT_NV12) != 0;
+  HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true, nv12));
   HZ_TRY(check_stream_id(c, stream_id));
-  if (flags & ~uint32_t(HZ_IO_HOST)) return fail(c, HZ_EINVAL, "unknown flags");
   int oW, oH;
   out_dims(c->prm, W, H, oW, oH);
-  if (n_frames > 1 && (in_frame_stride < in_pitch * size_t(H - 1) + size_t(3) * W ||
+  // input rows per frame (NV12: H luma rows and H/2 chroma rows) and bytes per row
+  const int in_rows = nv12 ? H + H / 2 : H;
+  const size_t in_row = nv12 ? size_t(W) : size_t(3) * W;
+  if (n_frames > 1 && (in_frame_stride < in_pitch * size_t(in_rows - 1) + in_row ||
                        out_frame_stride < out_pitch * size_t(oH - 1) + size_t(3) * oW))
     return fail(c, HZ_EINVAL, "frame stride smaller than a frame");
   if (n_frames == 0) return HZ_OK;
@@ -896,7 +908,7 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
     std::vector<hz_frame_desc> fr(n_frames);
     for (int f = 0; f < n_frames; ++f)
       fr[f] = hz_frame_desc{in + size_t(f) * in_frame_stride, in_pitch, out + size_t(f) * out_frame_stride,
-                            out_pitch, W, H, stream_id, 0u};
+                            out_pitch, W, H, stream_id, flags & HZ_INPUT_NV12};
     auto body = [&](cudaStream_t st) -> hz_status {
       if (chain) HZ_CK(c, cudaMemsetAsync(chain, 0, sizeof(HzStreamState), st));
       return video_device(c, fr.data(), n_frames, st, infos, chain);
@@ -914,11 +926,11 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
   // pairs; the H2D copy of wave k+1 (copy_in), the compute of wave k (s) and
   // the D2H copy of wave k-1 (copy_out) overlap, so both link directions stay
   // busy. Frames that are contiguous on the host move in one copy per wave.
-  const size_t fin = size_t(3) * W * H, fout = size_t(3) * oW * oH;
+  const size_t fin = in_row * size_t(in_rows), fout = size_t(3) * oW * oH;
   int G = (int)std::max<size_t>(1, HOSTIO_WAVE_BYTES / std::max<size_t>(fin, 1));
   G = std::min(G, MAXJ);
   G = std::min(G, n_frames);
-  const bool in_contig = in_pitch == size_t(3) * W && in_frame_stride == fin;
+  const bool in_contig = in_pitch == in_row && in_frame_stride == fin;
   const bool out_contig = out_pitch == size_t(3) * oW && out_frame_stride == fout;
   const size_t half = align_up(size_t(G) * (fin + fout), 4096);
   HZ_TRY(arena_reserve(c, c->stage, HOSTIO_BUFS * half, s));
@@ -938,15 +950,15 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
       HZ_CK(c, cudaMemcpyAsync(din, in + size_t(f0) * fin, size_t(m) * fin, cudaMemcpyHostToDevice, c->copy_in));
     } else {
       for (int k = 0; k < m; ++k)
-        HZ_CK(c, cudaMemcpy2DAsync(din + size_t(k) * fin, size_t(3) * W, in + size_t(f0 + k) * in_frame_stride,
-                                   in_pitch, size_t(3) * W, H, cudaMemcpyHostToDevice, c->copy_in));
+        HZ_CK(c, cudaMemcpy2DAsync(din + size_t(k) * fin, in_row, in + size_t(f0 + k) * in_frame_stride,
+                                   in_pitch, in_row, in_rows, cudaMemcpyHostToDevice, c->copy_in));
     }
     HZ_CK(c, cudaEventRecord(c->ev_in[b], c->copy_in));
     HZ_CK(c, cudaStreamWaitEvent(s, c->ev_in[b], 0));
     std::vector<hz_frame_desc> fr(m);
     for (int k = 0; k < m; ++k)
-      fr[k] = hz_frame_desc{din + size_t(k) * fin, size_t(3) * W, dout + size_t(k) * fout, size_t(3) * oW, W, H,
-                            stream_id, 0u};
+      fr[k] = hz_frame_desc{din + size_t(k) * fin, in_row, dout + size_t(k) * fout, size_t(3) * oW, W, H,
+                            stream_id, flags & HZ_INPUT_NV12};
     HZ_TRY(video_device(c, fr.data(), m, s, infos ? infos + f0 : nullptr, chain));
     HZ_CK(c, cudaEventRecord(c->ev_comp[b], s));
     HZ_CK(c, cudaStreamWaitEvent(c->copy_out, c->ev_comp[b], 0));
@@ -1001,7 +1013,7 @@ extern "C" hz_status hz_resize(hz_ctx* c, const uint8_t* in, int32_t W, int32_t 
   HZ_TRY(order_after_previous(c, s));
   ResizeJobs rj;
   rj.n = 1;
-  rj.j[0] = ResizeJob{in, (long long)in_pitch, out, (long long)out_pitch, W, H, W2, H2};
+  rj.j[0] = ResizeJob{in, (long long)in_pitch, out, (long long)out_pitch, W, H, W2, H2, 0, 0};
   {
     LaunchScope ls(c, HZ_K_RESIZE, s);
     k_resize<<<dim3(unsigned((size_t(W2) * H2 + 255) / 256), 1), 256, 0, s>>>(rj);
@@ -1194,8 +1206,9 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   if (!c) return HZ_EINVAL;
   if (n <= 0 || !frames) return fail(c, HZ_EINVAL, "bad frame list");
   for (int i = 0; i < n; ++i) {
+    if (frames[i].flags & ~uint32_t(HZ_GUIDED | HZ_INPUT_NV12)) return fail(c, HZ_EINVAL, "unknown frame flags");
     HZ_TRY(check_frame(c, frames[i].in, frames[i].W, frames[i].H, frames[i].in_pitch, frames[i].out,
-                       frames[i].out_pitch, true, true));
+                       frames[i].out_pitch, true, true, (frames[i].flags & HZ_INPUT_NV12) != 0));
     HZ_TRY(check_stream_id(c, frames[i].stream_id));
   }
   constexpr int NCAND = int(sizeof TUNE_WAVE_MIB / sizeof TUNE_WAVE_MIB[0]);

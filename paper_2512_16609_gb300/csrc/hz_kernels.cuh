@@ -90,6 +90,8 @@ struct ResizeJob {
   uint8_t* dst;
   long long dst_pitch;
   int sW, sH, dW, dH;
+  int nv12;  // the source is NV12 (Y plane, then the Cb/Cr plane at src + src_pitch * sH)
+  int pad;
 };
 struct ResizeJobs {
   int n;
@@ -110,6 +112,28 @@ __device__ __forceinline__ void resize_taps(int i, int n_in, int n_out, int& i0,
   i1 = min(i0 + 1, n_in - 1);
 }
 
+// RGB of source pixel (x, y). NV12: BT.601 limited range with the 8-bit
+// integer coefficients, C = Y - 16, D = Cb - 128, E = Cr - 128,
+// R = (298 C + 409 E + 128) >> 8, G = (298 C - 100 D - 208 E + 128) >> 8,
+// B = (298 C + 516 D + 128) >> 8 (arithmetic shifts), clipped to [0, 255];
+// the chroma sample of (x, y) is (x / 2, y / 2).
+__device__ __forceinline__ void src_rgb(const ResizeJob& r, int x, int y, int (&v)[3]) {
+  if (r.nv12) {
+    const int C = int(__ldg(r.src + (long long)y * r.src_pitch + x)) - 16;
+    const uint8_t* uv = r.src + (long long)(r.sH + (y >> 1)) * r.src_pitch + 2 * (x >> 1);
+    const int D = int(__ldg(uv)) - 128, E = int(__ldg(uv + 1)) - 128;
+    v[0] = min(max((298 * C + 409 * E + 128) >> 8, 0), 255);
+    v[1] = min(max((298 * C - 100 * D - 208 * E + 128) >> 8, 0), 255);
+    v[2] = min(max((298 * C + 516 * D + 128) >> 8, 0), 255);
+  } else {
+    const uint8_t* p = r.src + (long long)y * r.src_pitch + 3LL * x;
+    v[0] = __ldg(p);
+    v[1] = __ldg(p + 1);
+    v[2] = __ldg(p + 2);
+  }
+}
+
+// Input preparation: NV12 conversion and/or resize into the plan buffer.
 __global__ void __launch_bounds__(256) k_resize(const __grid_constant__ ResizeJobs jobs) {
   const ResizeJob& r = jobs.j[blockIdx.y];
   const unsigned i = blockIdx.x * 256u + threadIdx.x;
@@ -118,13 +142,16 @@ __global__ void __launch_bounds__(256) k_resize(const __grid_constant__ ResizeJo
   int x0, x1, wx, y0, y1, wy;
   resize_taps(x, r.sW, r.dW, x0, x1, wx);
   resize_taps(y, r.sH, r.dH, y0, y1, wy);
-  const uint8_t* a = r.src + (long long)y0 * r.src_pitch;
-  const uint8_t* b = r.src + (long long)y1 * r.src_pitch;
+  int p00[3], p01[3], p10[3], p11[3];
+  src_rgb(r, x0, y0, p00);
+  src_rgb(r, x1, y0, p01);
+  src_rgb(r, x0, y1, p10);
+  src_rgb(r, x1, y1, p11);
   uint8_t* o = r.dst + (long long)y * r.dst_pitch + 3LL * x;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const int top = (256 - wx) * int(__ldg(a + 3 * x0 + c)) + wx * int(__ldg(a + 3 * x1 + c));
-    const int bot = (256 - wx) * int(__ldg(b + 3 * x0 + c)) + wx * int(__ldg(b + 3 * x1 + c));
+    const int top = (256 - wx) * p00[c] + wx * p01[c];
+    const int bot = (256 - wx) * p10[c] + wx * p11[c];
     o[c] = uint8_t(((256 - wy) * top + wy * bot + (1 << 15)) >> 16);
   }
 }

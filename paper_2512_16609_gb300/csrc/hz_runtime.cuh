@@ -130,8 +130,9 @@ struct FramePlan {
   long long plane_pitch32, plane_pitch16;
   size_t off_copy;                          // aligned copy of an unaligned input, or the resized
   long long copy_pitch;                     // frame (0 if none)
-  int in_W = 0, in_H = 0;                   // input size of a resized frame
+  int in_W = 0, in_H = 0;                   // input size (of a resized or converted frame)
   bool resized = false;                     // W x H is the processing size, input is in_W x in_H
+  bool nv12 = false;                        // the input is NV12 (converted into the plan buffer)
 };
 
 struct LaunchPlan {
@@ -175,11 +176,10 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     f.W = Ws[i];
     f.H = Hs[i];
     f.resized = resize && prm.proc_width > 0;
-    if (f.resized) {
-      f.in_W = Ws[i];
-      f.in_H = Hs[i];
-      out_dims(prm, Ws[i], Hs[i], f.W, f.H);
-    }
+    f.nv12 = fr && (fr[i].flags & HZ_INPUT_NV12);
+    f.in_W = Ws[i];
+    f.in_H = Hs[i];
+    if (f.resized) out_dims(prm, Ws[i], Hs[i], f.W, f.H);
     f.band_h = p1_band_rows(prm.patch / 2);
     f.tiles_x = (f.W + P1_SW - 1) / P1_SW;
     f.tiles_y = (f.H + f.band_h - 1) / f.band_h;
@@ -207,7 +207,7 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     }
     f.off_copy = 0;
     f.copy_pitch = 0;
-    if (f.resized || (fr && !input_aligned16(fr[i].in, fr[i].in_pitch))) {
+    if (f.resized || f.nv12 || (fr && !input_aligned16(fr[i].in, fr[i].in_pitch))) {
       f.copy_pitch = (long long)align_up(size_t(3) * f.W, 16);
       f.off_copy = o;
       o = align_up(o + size_t(f.copy_pitch) * f.H, 1024);

@@ -114,6 +114,11 @@ static void complete_loop(Server* S) {
   }
 }
 
+// Bytes of a request's input frame, packed (NV12: W x 3H/2, else 3W x H).
+static size_t in_bytes(const hz_ctx* c, const Request& r) {
+  return (c->stream_flags[r.sid] & HZ_INPUT_NV12) ? size_t(r.W) * (r.H + r.H / 2) : size_t(3) * r.W * r.H;
+}
+
 // Enqueue one batch on the slot: H2D of host frames, the batched launch,
 // D2H of host outputs and of the records. Returns the launch status.
 static hz_status launch_batch(Server* S, Slot& sl) {
@@ -124,7 +129,7 @@ static hz_status launch_batch(Server* S, Slot& sl) {
     if (r.flags & HZ_IO_HOST) {
       int oW, oH;
       out_dims(c->prm, r.W, r.H, oW, oH);
-      need += align_up(size_t(3) * r.W * r.H, 256) + align_up(size_t(3) * oW * oH, 256);
+      need += align_up(in_bytes(c, r), 256) + align_up(size_t(3) * oW * oH, 256);
     }
   if (need > sl.stage.cap) {
     if (sl.stage.base) cudaFree(sl.stage.base);
@@ -143,20 +148,22 @@ static hz_status launch_batch(Server* S, Slot& sl) {
   bool any_host = false;
   for (int i = 0; i < n; ++i) {
     const Request& r = sl.reqs[i];
+    const bool nv12 = (c->stream_flags[r.sid] & HZ_INPUT_NV12) != 0;
     fr[i] = hz_frame_desc{r.in, r.in_pitch, r.out, r.out_pitch, r.W, r.H, r.sid,
-                          c->stream_flags[r.sid] & HZ_GUIDED};
+                          c->stream_flags[r.sid] & (HZ_GUIDED | HZ_INPUT_NV12)};
     if (r.flags & HZ_IO_HOST) {
       any_host = true;
       int oW, oH;
       out_dims(c->prm, r.W, r.H, oW, oH);
-      const size_t fb = align_up(size_t(3) * r.W * r.H, 256);
+      const size_t fb = align_up(in_bytes(c, r), 256);
+      const size_t row = nv12 ? size_t(r.W) : size_t(3) * r.W;
       uint8_t* din = sl.stage.base + o;
       uint8_t* dout = din + fb;
       o += fb + align_up(size_t(3) * oW * oH, 256);
-      HZ_CK(c, cudaMemcpy2DAsync(din, size_t(3) * r.W, r.in, r.in_pitch, size_t(3) * r.W, r.H,
+      HZ_CK(c, cudaMemcpy2DAsync(din, row, r.in, r.in_pitch, row, nv12 ? r.H + r.H / 2 : r.H,
                                  cudaMemcpyHostToDevice, S->s_h2d));
       fr[i].in = din;
-      fr[i].in_pitch = size_t(3) * r.W;
+      fr[i].in_pitch = row;
       fr[i].out = dout;
       fr[i].out_pitch = size_t(3) * oW;
     }
@@ -300,14 +307,16 @@ static size_t stream_footprint(const hz_params& prm, int W, int H, unsigned flag
   // resident scratch of one frame in flight plus in/out staging
   int oW, oH;
   out_dims(prm, W, H, oW, oH);
-  return lp.total + align_up(size_t(3) * W * H, 4096) + align_up(size_t(3) * oW * oH, 4096);
+  const size_t in = (flags & HZ_INPUT_NV12) ? size_t(W) * (H + H / 2) : size_t(3) * W * H;
+  return lp.total + align_up(in, 4096) + align_up(size_t(3) * oW * oH, 4096);
 }
 
 extern "C" hz_status hz_open_stream(hz_ctx* c, int32_t W, int32_t H, uint32_t flags, int32_t* stream_id) {
   if (!c || !stream_id) return HZ_EINVAL;
   if (W < 1 || H < 1 || W > HZ_MAX_DIM || H > HZ_MAX_DIM || (long long)W * H > (1LL << 28))
     return fail(c, HZ_EINVAL, "frame size %dx%d out of range", W, H);
-  if (flags & ~uint32_t(HZ_GUIDED)) return fail(c, HZ_EINVAL, "unknown stream flags");
+  if (flags & ~uint32_t(HZ_GUIDED | HZ_INPUT_NV12)) return fail(c, HZ_EINVAL, "unknown stream flags");
+  if ((flags & HZ_INPUT_NV12) && ((W | H) & 1)) return fail(c, HZ_EINVAL, "NV12 streams need even sizes");
   const size_t need = stream_footprint(c->prm, W, H, flags);
   std::lock_guard<std::mutex> lk(c->smu);
   int sid = -1;
@@ -386,15 +395,18 @@ extern "C" hz_status hz_submit(hz_ctx* c, int32_t sid, const uint8_t* in, size_t
   if (!c || !ticket) return HZ_EINVAL;
   if (flags & ~uint32_t(HZ_IO_HOST)) return fail(c, HZ_EINVAL, "unknown submit flags");
   int W, H;
+  unsigned sflags;
   {
     std::lock_guard<std::mutex> lk(c->smu);
     if (sid < 0 || sid >= MAX_STREAMS || !c->stream_open[sid]) return fail(c, HZ_EINVAL, "stream %d is not open", sid);
     W = c->stream_W[sid];
     H = c->stream_H[sid];
+    sflags = c->stream_flags[sid];
   }
   int oW, oH;
   out_dims(c->prm, W, H, oW, oH);
-  if (!in || !out || in_pitch < size_t(3) * W || out_pitch < size_t(3) * oW)
+  const size_t in_row = (sflags & HZ_INPUT_NV12) ? size_t(W) : size_t(3) * W;
+  if (!in || !out || in_pitch < in_row || out_pitch < size_t(3) * oW)
     return fail(c, HZ_EINVAL, "bad buffers for a %dx%d stream", W, H);
   {
     std::lock_guard<std::mutex> lk(c->smu);
