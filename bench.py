@@ -220,6 +220,54 @@ def tune_wave_bytes(hzp, ctx, inp, out, choice):
             "tuner": "hz_autotune_wave_bytes"}
 
 
+def run_variants(hzp, dev, frames_np, reps=10):
+    """The extension rows on the 300-frame 1080p sequence, device-resident,
+    CUDA events over `reps` calls after three warm-up calls each: the
+    processing-size front-end (1080p in, 640x480 dehazed out), adaptive
+    gamma, and NV12 camera input (30 distinct frames converted once and
+    tiled to 300)."""
+    import torch
+    out = {}
+    inp = torch.from_numpy(frames_np).to(dev)
+    n = inp.shape[0]
+
+    def timed(ctx, a, b, flags=0):
+        for _ in range(3):
+            hzp.hz_dehaze_video(ctx, a, b, flags=flags)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            hzp.hz_dehaze_video(ctx, a, b, flags=flags)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    cases = [("resize_1080p_to_640x480", dict(airlight_ema=0.9, proc_width=640, proc_height=480), (480, 640), 0),
+             ("adaptive_gamma", dict(airlight_ema=0.9, adaptive_gamma=1), (H, W), 0),
+             ("fast_transmission_eq4", dict(airlight_ema=0.9, t_mode=1, omega=0.5, t0=0.05), (H, W), 0)]
+    for name, kw, (oh, ow), flags in cases:
+        ctx = hzp.hz_create(hzp.params(**kw), dev.index)
+        try:
+            hzp.hz_set_wave_bytes(ctx, 256 << 20)
+            o = torch.empty((n, oh, ow, 3), dtype=torch.uint8, device=dev)
+            ms = timed(ctx, inp, o, flags)
+            out[name] = {"ms_per_step": ms, "frames_per_s": n / (ms / 1e3)}
+        finally:
+            hzp.hz_destroy(ctx)
+    nv = np.stack([hazegen.rgb_to_nv12(frames_np[f]) for f in range(30)])
+    nv_dev = torch.from_numpy(np.concatenate([nv] * (n // 30 + 1))[:n]).to(dev)
+    ctx = hzp.hz_create(hzp.params(airlight_ema=0.9), dev.index)
+    try:
+        hzp.hz_set_wave_bytes(ctx, 256 << 20)
+        o = torch.empty_like(inp)
+        ms = timed(ctx, nv_dev, o, hzp.HZ_INPUT_NV12)
+        out["nv12_input_1080p"] = {"ms_per_step": ms, "frames_per_s": n / (ms / 1e3)}
+    finally:
+        hzp.hz_destroy(ctx)
+    return out
+
+
 BATCH_SPECS = hazegen.mixed_batch_specs(16, 100)  # 16 each of 854x480, 1280x720, 1920x1080, 3840x2160
 
 
@@ -288,6 +336,7 @@ def main():
                     help="input MiB per wave of frames, or 'auto' for the library autotuner's pick")
     ap.add_argument("--no-graphs", action="store_true", help="time direct calls instead of graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-size batch measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the resize / adaptive gamma / NV12 lines")
     ap.add_argument("--frames", type=int, default=300,
                     help="frames per step; only profiling runs change it from the 300-frame workload")
     args = ap.parse_args()
@@ -400,6 +449,10 @@ def main():
     if batch_inputs is not None:
         batch = run_batch_mixed(hzp, dev, batch_inputs)
 
+    variants = None
+    if not args.no_variants and rank == 0 and ws == 1:
+        variants = run_variants(hzp, dev, frames_np)
+
     served = None
     if served_inputs is not None:
         served = run_served(hzp, dev, served_inputs, args.served_seconds)
@@ -414,7 +467,7 @@ def main():
     hzp.hz_destroy(ctx)
     if rank == 0:
         emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-             launches, clocks, served, tuning, batch, graphs=not args.no_graphs)
+             launches, clocks, served, tuning, batch, graphs=not args.no_graphs, variants=variants)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -585,7 +638,7 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
 
 
 def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-         launches, clocks, served=None, tuning=None, batch=None, graphs=False):
+         launches, clocks, served=None, tuning=None, batch=None, graphs=False, variants=None):
     if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -610,6 +663,7 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
             "clocks": clocks.summary(),
             "serving": served,
             "batch_mixed": batch,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
 

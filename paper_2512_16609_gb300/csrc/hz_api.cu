@@ -143,13 +143,15 @@ cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n,
 // buffers (one launch for all of them), unaligned ones are copied.
 hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base,
                          cudaStream_t s) {
-  ResizeJobs rj;
-  rj.n = 0;
-  unsigned most = 0;
+  ResizeJobs rj, cj;  // resize (any format), NV12 conversion at the same size
+  rj.n = cj.n = 0;
+  unsigned most = 0, most_c = 0;
   for (int i = 0; i < n; ++i) {
     const FramePlan& f = lp.fp[i];
     if (f.resized || f.nv12) {
-      ResizeJob& r = rj.j[rj.n++];
+      const bool same = !f.resized;
+      ResizeJob& r = same ? cj.j[cj.n++] : rj.j[rj.n++];
+      if (same) most_c = std::max(most_c, unsigned((f.W + 15) / 16) * unsigned(f.H));
       r.src = fr[i].in;
       r.src_pitch = (long long)fr[i].in_pitch;
       r.dst = base + f.off_copy;
@@ -160,7 +162,7 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
       r.dH = f.H;
       r.nv12 = f.nv12 ? 1 : 0;
       r.pad = 0;
-      most = std::max(most, unsigned(f.W) * unsigned(f.H));
+      if (!same) most = std::max(most, unsigned(f.W) * unsigned(f.H));
     } else if (f.off_copy) {
       HZ_CK(c, cudaMemcpy2DAsync(base + f.off_copy, size_t(f.copy_pitch), fr[i].in, fr[i].in_pitch,
                                  size_t(3) * f.W, size_t(f.H), cudaMemcpyDeviceToDevice, s));
@@ -169,6 +171,11 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
   if (rj.n) {
     LaunchScope ls(c, HZ_K_RESIZE, s);
     k_resize<<<dim3((most + 255) / 256, rj.n), 256, 0, s>>>(rj);
+    HZ_CK(c, cudaGetLastError());
+  }
+  if (cj.n) {
+    LaunchScope ls(c, HZ_K_RESIZE, s);
+    k_nv12_rgb<<<dim3((most_c + 255) / 256, cj.n), 256, 0, s>>>(cj);
     HZ_CK(c, cudaGetLastError());
   }
   return HZ_OK;
