@@ -123,22 +123,23 @@ __global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
 }
 
 // Horizontal window sums of the vertical sums; each thread produces GF_HRUN
-// consecutive outputs of one row from a shared-memory copy of the row.
+// consecutive outputs of one row from a shared-memory copy of the row
+// (padded so that the threads' runs read distinct banks).
 template <int PASS>
 __global__ void __launch_bounds__(GF_HSEG / GF_HRUN) k_gf_h(const GfArgs g) {
   constexpr int NQ = (PASS == 1) ? 4 : 2;
   constexpr int NT = GF_HSEG / GF_HRUN;
-  extern __shared__ float srow[];  // [NQ][GF_HSEG + 2r]
+  extern __shared__ float srow[];  // [NQ][gf_sidx(GF_HSEG + 2r)]
   const int y = blockIdx.y;
   const int xs0 = blockIdx.x * GF_HSEG;
   const int W = g.W, H = g.H, r = g.r;
-  const int span = GF_HSEG + 2 * r;
+  const int span = gf_sidx(GF_HSEG + 2 * r);
   const long long plane = (long long)W * H;
-  for (int i = threadIdx.x; i < span; i += NT) {
+  for (int i = threadIdx.x; i < GF_HSEG + 2 * r; i += NT) {
     const int x = xs0 - r + i;
     const bool in = (x >= 0 && x < W);
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) srow[k * span + i] = in ? g.vs[k * plane + (long long)y * W + x] : 0.f;
+    for (int k = 0; k < NQ; ++k) srow[k * span + gf_sidx(i)] = in ? g.vs[k * plane + (long long)y * W + x] : 0.f;
   }
   __syncthreads();
   const int xf = xs0 + threadIdx.x * GF_HRUN;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(GF_HSEG / GF_HRUN) k_gf_h(const GfArgs g) {
   const int li = xf - xs0;  // local index of x in srow is li + r
   for (int j = li; j <= li + 2 * r; ++j) {
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) s[k].add(srow[k * span + j]);
+    for (int k = 0; k < NQ; ++k) s[k].add(srow[k * span + gf_sidx(j)]);
   }
   for (int o = 0; o < GF_HRUN; ++o) {
     const int x = xf + o;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(GF_HSEG / GF_HRUN) k_gf_h(const GfArgs g) {
       st_plane(g.q, g.q_pitch, g.q_half, y, x, qv);
     }
     if (o + 1 < GF_HRUN) {
-      const int jin = li + o + 2 * r + 1, jout = li + o;
+      const int jin = gf_sidx(li + o + 2 * r + 1), jout = gf_sidx(li + o);
 #pragma unroll
       for (int k = 0; k < NQ; ++k) {
         s[k].add(srow[k * span + jin]);

@@ -39,10 +39,13 @@ inline __host__ __device__ int p3_units(int W, int H) {
   return int((groups + P3_THREADS - 1) / P3_THREADS);
 }
 // ---- guided filter ------------------------------------------------------
-constexpr int GF_VBAND = 64;    // output rows per vertical-pass block
-constexpr int GF_VCOLS = 128;   // columns per vertical-pass block
-constexpr int GF_HSEG = 256;    // outputs per horizontal-pass block
-constexpr int GF_HRUN = 8;      // consecutive outputs per thread
+constexpr int GF_VBAND = 128;   // output rows per vertical-pass block
+constexpr int GF_VCOLS = 64;    // columns per vertical-pass block
+constexpr int GF_HSEG = 2048;   // outputs per horizontal-pass block
+constexpr int GF_HRUN = 32;     // consecutive outputs per thread
+// shared-memory index of row element i in the horizontal pass: one pad word
+// per 32, so that threads GF_HRUN elements apart fall in different banks
+__host__ __device__ constexpr int gf_sidx(int i) { return i + (i >> 5); }
 
 constexpr float A_FLOOR = 1e-6f;  // airlight floor used in ratios I/A
 constexpr int HZ_STATUS_SELECT_FAILED = -100;  // per-frame status: selection inconsistent
