@@ -245,8 +245,8 @@ hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool bal
 static hz_status run_guided(hz_ctx* c, GfArgs& g, cudaStream_t s) {
   const dim3 gv((g.W + GF_VCOLS - 1) / GF_VCOLS, (g.H + GF_VBAND - 1) / GF_VBAND);
   const dim3 gh((g.W + GF_HSEG - 1) / GF_HSEG, g.H);
-  const size_t sm1 = sizeof(float) * 4 * gf_sidx(GF_HSEG + 2 * g.r);
-  const size_t sm2 = sizeof(float) * 2 * gf_sidx(GF_HSEG + 2 * g.r);
+  const size_t sm1 = sizeof(float) * 4 * (gf_sidx(GF_HSEG + 2 * g.r) + gf_sidx(GF_HSEG));
+  const size_t sm2 = sizeof(float) * 2 * (gf_sidx(GF_HSEG + 2 * g.r) + gf_sidx(GF_HSEG));
   HZ_CK(c, cudaFuncSetAttribute(k_gf_h<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
   HZ_CK(c, cudaFuncSetAttribute(k_gf_h<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   {
@@ -256,7 +256,7 @@ static hz_status run_guided(hz_ctx* c, GfArgs& g, cudaStream_t s) {
   HZ_CK(c, cudaGetLastError());
   {
     LaunchScope ls(c, HZ_K_GUIDED, s);
-    k_gf_h<1><<<gh, GF_HSEG / GF_HRUN, sm1, s>>>(g);
+    k_gf_h<1><<<gh, GF_HT, sm1, s>>>(g);
   }
   HZ_CK(c, cudaGetLastError());
   {
@@ -266,7 +266,7 @@ static hz_status run_guided(hz_ctx* c, GfArgs& g, cudaStream_t s) {
   HZ_CK(c, cudaGetLastError());
   {
     LaunchScope ls(c, HZ_K_GUIDED, s);
-    k_gf_h<2><<<gh, GF_HSEG / GF_HRUN, sm2, s>>>(g);
+    k_gf_h<2><<<gh, GF_HT, sm2, s>>>(g);
   }
   HZ_CK(c, cudaGetLastError());
   return HZ_OK;

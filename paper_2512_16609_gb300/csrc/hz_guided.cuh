@@ -85,9 +85,12 @@ __device__ __forceinline__ void gf_quant(const GfArgs& g, int y, int x, float (&
 }
 
 // Vertical window sums, thread per column, GF_VBAND output rows per block.
+// Rows are read GF_VU at a time (all loads issued before the sums use them)
+// so that each thread keeps several rows in flight.
 template <int PASS>
 __global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
   constexpr int NQ = (PASS == 1) ? 4 : 2;
+  constexpr int U = GF_VU;
   const int x = blockIdx.x * GF_VCOLS + threadIdx.x;
   const int y0 = blockIdx.y * GF_VBAND;
   if (x >= g.W || y0 >= g.H) return;
@@ -96,71 +99,99 @@ __global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
 #pragma unroll
   for (int k = 0; k < NQ; ++k) s[k].init();
   const int ya = max(0, y0 - r), yb = min(H - 1, y0 + r);
-  for (int y = ya; y <= yb; ++y) {
-    float q[4];
-    gf_quant<PASS>(g, y, x, q);
+  for (int y = ya; y <= yb; y += U) {
+    float q[U][4];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) s[k].add(q[k]);
+    for (int u = 0; u < U; ++u)
+      if (y + u <= yb) gf_quant<PASS>(g, y + u, x, q[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (y + u <= yb) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) s[k].add(q[u][k]);
+      }
   }
   const long long plane = (long long)g.W * g.H;
   const int y1 = min(H, y0 + GF_VBAND);
-  for (int y = y0; y < y1; ++y) {
+  for (int y = y0; y < y1; y += U) {
+    float qi[U][4], qo[U][4];
 #pragma unroll
-    for (int k = 0; k < NQ; ++k) g.vs[k * plane + (long long)y * g.W + x] = s[k].get();
-    const int yin = y + r + 1, yout = y - r;
-    float q[4];
-    if (yin < H) {
-      gf_quant<PASS>(g, yin, x, q);
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) s[k].add(q[k]);
+    for (int u = 0; u < U; ++u) {
+      const int yin = y + u + r + 1, yout = y + u - r;
+      const bool live = y + u < y1;
+      if (live && yin < H) gf_quant<PASS>(g, yin, x, qi[u]);
+      else qi[u][0] = qi[u][1] = qi[u][2] = qi[u][3] = 0.f;
+      if (live && yout >= 0) gf_quant<PASS>(g, yout, x, qo[u]);
+      else qo[u][0] = qo[u][1] = qo[u][2] = qo[u][3] = 0.f;
     }
-    if (yout >= 0) {
-      gf_quant<PASS>(g, yout, x, q);
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) s[k].add(-q[k]);
+    for (int u = 0; u < U; ++u) {
+      if (y + u >= y1) break;
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        g.vs[k * plane + (long long)(y + u) * g.W + x] = s[k].get();
+        s[k].add(qi[u][k]);
+        s[k].add(-qo[u][k]);
+      }
     }
   }
 }
 
-// Horizontal window sums of the vertical sums; each thread produces GF_HRUN
-// consecutive outputs of one row from a shared-memory copy of the row
-// (padded so that the threads' runs read distinct banks).
+// Horizontal window sums of the vertical sums for GF_HSEG outputs of one
+// row, in three phases: the block copies the row segment and its halo into
+// shared memory (padded so that threads GF_HRUN elements apart use distinct
+// banks); each thread slides one quantity's window along one run of GF_HRUN
+// outputs (compensated sums, restarted per run) into a shared sums array;
+// then the block forms a and b (pass 1) or q (pass 2) per output and writes
+// them out coalesced.
 template <int PASS>
-__global__ void __launch_bounds__(GF_HSEG / GF_HRUN) k_gf_h(const GfArgs g) {
+__global__ void __launch_bounds__(GF_HT) k_gf_h(const GfArgs g) {
   constexpr int NQ = (PASS == 1) ? 4 : 2;
-  constexpr int NT = GF_HSEG / GF_HRUN;
-  extern __shared__ float srow[];  // [NQ][gf_sidx(GF_HSEG + 2r)]
+  constexpr int NRUN = GF_HSEG / GF_HRUN;
+  extern __shared__ float smem_gf[];
   const int y = blockIdx.y;
   const int xs0 = blockIdx.x * GF_HSEG;
   const int W = g.W, H = g.H, r = g.r;
   const int span = gf_sidx(GF_HSEG + 2 * r);
+  float* srow = smem_gf;                  // [NQ][span]
+  constexpr int SS = gf_sidx(GF_HSEG);    // padded stride of the sums
+  float* ssum = smem_gf + NQ * span;      // [NQ][SS], element o at gf_sidx(o)
   const long long plane = (long long)W * H;
-  for (int i = threadIdx.x; i < GF_HSEG + 2 * r; i += NT) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < GF_HSEG + 2 * r; i += GF_HT) {
     const int x = xs0 - r + i;
     const bool in = (x >= 0 && x < W);
 #pragma unroll
     for (int k = 0; k < NQ; ++k) srow[k * span + gf_sidx(i)] = in ? g.vs[k * plane + (long long)y * W + x] : 0.f;
   }
   __syncthreads();
-  const int xf = xs0 + threadIdx.x * GF_HRUN;
-  if (xf >= W) return;
-  const int cy = min(H - 1, y + r) - max(0, y - r) + 1;
-  Neu s[NQ];
-#pragma unroll
-  for (int k = 0; k < NQ; ++k) s[k].init();
-  const int li = xf - xs0;  // local index of x in srow is li + r
-  for (int j = li; j <= li + 2 * r; ++j) {
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) s[k].add(srow[k * span + gf_sidx(j)]);
+  for (int w = tid; w < NRUN * NQ; w += GF_HT) {
+    const int run = w % NRUN, k = w / NRUN;
+    const int li = run * GF_HRUN;
+    if (xs0 + li >= W) continue;
+    const float* sr = srow + k * span;
+    Neu sm;
+    sm.init();
+    for (int j = li; j <= li + 2 * r; ++j) sm.add(sr[gf_sidx(j)]);
+    float* out = ssum + k * SS;
+#pragma unroll 4
+    for (int o = 0; o < GF_HRUN; ++o) {
+      out[gf_sidx(li + o)] = sm.get();
+      sm.add(sr[gf_sidx(li + o + 2 * r + 1)]);
+      sm.add(-sr[gf_sidx(li + o)]);
+    }
   }
-  for (int o = 0; o < GF_HRUN; ++o) {
-    const int x = xf + o;
+  __syncthreads();
+  const int cy = min(H - 1, y + r) - max(0, y - r) + 1;
+  for (int o = tid; o < GF_HSEG; o += GF_HT) {
+    const int x = xs0 + o;
     if (x >= W) break;
     const int cx = min(W - 1, x + r) - max(0, x - r) + 1;
     const float inv = 1.f / float(cx * cy);
     if constexpr (PASS == 1) {
-      const float m0 = s[0].get() * inv, m1 = s[1].get() * inv;
-      const float m2 = s[2].get() * inv, m3 = s[3].get() * inv;
+      const int so = gf_sidx(o);
+      const float m0 = ssum[so] * inv, m1 = ssum[SS + so] * inv;
+      const float m2 = ssum[2 * SS + so] * inv, m3 = ssum[3 * SS + so] * inv;
       const float var = m2 - m0 * m0;
       const float cov = m3 - m0 * m1;
       const float a = cov / (var + g.eps);
@@ -168,19 +199,12 @@ __global__ void __launch_bounds__(GF_HSEG / GF_HRUN) k_gf_h(const GfArgs g) {
       st_plane(g.a, g.ab_pitch, g.ab_half, y, x, a);
       st_plane(g.b, g.ab_pitch, g.ab_half, y, x, b);
     } else {
-      const float ma = s[0].get() * inv, mb = s[1].get() * inv;
+      const int so = gf_sidx(o);
+      const float ma = ssum[so] * inv, mb = ssum[SS + so] * inv;
       const float gv = gray_of(g.in + (long long)y * g.in_pitch + 3LL * x);
       float qv = fmaf(ma, gv, mb);
       if (g.clamp) qv = fminf(fmaxf(qv, g.t0), 1.f);
       st_plane(g.q, g.q_pitch, g.q_half, y, x, qv);
-    }
-    if (o + 1 < GF_HRUN) {
-      const int jin = gf_sidx(li + o + 2 * r + 1), jout = gf_sidx(li + o);
-#pragma unroll
-      for (int k = 0; k < NQ; ++k) {
-        s[k].add(srow[k * span + jin]);
-        s[k].add(-srow[k * span + jout]);
-      }
     }
   }
 }

@@ -41,8 +41,10 @@ inline __host__ __device__ int p3_units(int W, int H) {
 // ---- guided filter ------------------------------------------------------
 constexpr int GF_VBAND = 128;   // output rows per vertical-pass block
 constexpr int GF_VCOLS = 64;    // columns per vertical-pass block
+constexpr int GF_VU = 8;        // rows loaded together by a vertical-pass thread
 constexpr int GF_HSEG = 2048;   // outputs per horizontal-pass block
-constexpr int GF_HRUN = 32;     // consecutive outputs per thread
+constexpr int GF_HRUN = 32;     // consecutive outputs per sliding run
+constexpr int GF_HT = 256;      // threads per horizontal-pass block
 // shared-memory index of row element i in the horizontal pass: one pad word
 // per 32, so that threads GF_HRUN elements apart fall in different banks
 __host__ __device__ constexpr int gf_sidx(int i) { return i + (i >> 5); }
