@@ -40,7 +40,7 @@ inline __host__ __device__ int p3_units(int W, int H) {
 }
 // ---- guided filter ------------------------------------------------------
 constexpr int GF_VBAND = 128;   // output rows per vertical-pass block
-constexpr int GF_VCOLS = 64;    // columns per vertical-pass block
+constexpr int GF_VCOLS = 128;   // columns per vertical-pass block
 constexpr int GF_VU = 8;        // rows loaded together by a vertical-pass thread
 constexpr int GF_HSEG = 2048;   // outputs per horizontal-pass block
 constexpr int GF_HRUN = 32;     // consecutive outputs per sliding run
