@@ -178,6 +178,24 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_max_ms(ms, ws, device=None):
+    """The slowest replica's time: MAX all-reduce over the process group
+    (each replica's timed region is bracketed by barriers)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ms_max, ws, frames, steps):
+    """Frames/s of the whole job: every replica processed `frames` x `steps`
+    frames within the slowest replica's time."""
+    return ws * frames * steps / (ms_max / 1e3)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -451,13 +469,9 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = hzp.hz_get_profile(ctx, reset=True)
     launches = sum(v["launches"] for v in prof.values())
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = aggregate_max_ms(ms, ws, dev)
     ms_step = ms / args.steps
-    value = ws * F * args.steps / (ms / 1e3)
+    value = whole_job_value(ms, ws, F, args.steps)
 
     # ---- per-kernel device time with events on the library's stream ------
     hzp.hz_set_profiling(ctx, True)
