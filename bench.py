@@ -39,8 +39,7 @@ METRIC = "1080p frames/s"
 WORKLOAD = "video 300x1920x1080 RGB u8, patch 15, omega 0.95, t0 0.1, top 0.001, EMA 0.9"
 ALG_BYTES_PER_PX = 6.0  # read I once, write the output once
 # algorithmic bytes per pixel of each kernel class: what its inputs and
-# outputs must move once (dark: I in, P out; recon: I and P in, out written;
-# fused: the whole path, I in and out written)
+# outputs must move once (dark: I in, P out; recon: I and P in, out written)
 KERNEL_BYTES_PER_PX = {"dark": 6.0, "recon": 9.0, "select": 0.0, "airlight": 0.0}
 
 
