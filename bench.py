@@ -491,6 +491,7 @@ def main():
     # DRAM bytes per pixel of the top kernel from its ncu capture (a smaller
     # launch of the same kernel), scaled to this launch's pixels
     traffic = None
+    limiter = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
@@ -498,6 +499,7 @@ def main():
                 ent = json.load(f).get(top)
             if ent:
                 traffic = ent["bytes_per_px"] * px_launch
+                limiter = ent.get("limiter")
         except (OSError, ValueError, KeyError, TypeError):
             traffic = None
 
@@ -529,7 +531,8 @@ def main():
     hzp.hz_destroy(ctx)
     if rank == 0:
         emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-             launches, clocks, served, tuning, batch, graphs=not args.no_graphs, variants=variants)
+             launches, clocks, served, tuning, batch, graphs=not args.no_graphs, variants=variants,
+             limiter=limiter)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -700,7 +703,7 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
 
 
 def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-         launches, clocks, served=None, tuning=None, batch=None, graphs=False, variants=None):
+         launches, clocks, served=None, tuning=None, batch=None, graphs=False, variants=None, limiter=None):
     if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -717,7 +720,8 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "alg_bytes_per_px": KERNEL_BYTES_PER_PX.get(top, ALG_BYTES_PER_PX),
-                         "avg_launch_ms": avg_ms},
+                         "avg_launch_ms": avg_ms,
+                         "limiter_from_ncu": limiter},
             "kernels": {k: v for k, v in kprof.items() if v["launches"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
