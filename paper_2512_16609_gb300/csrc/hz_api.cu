@@ -251,7 +251,7 @@ static hz_status run_guided(hz_ctx* c, GfArgs& g, cudaStream_t s) {
   HZ_CK(c, cudaFuncSetAttribute(k_gf_h<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
   {
     LaunchScope ls(c, HZ_K_GUIDED, s);
-    k_gf_v<1><<<gv, GF_VCOLS, 0, s>>>(g);
+    k_gf_v<1><<<dim3(gv.x, gv.y, 2), GF_VCOLS, 0, s>>>(g);
   }
   HZ_CK(c, cudaGetLastError());
   {
@@ -892,6 +892,7 @@ extern "C" hz_status hz_dehaze_video(hz_ctx* c, int32_t stream_id, const uint8_t
                                      void* cuda_stream, hz_frame_info* infos) {
   if (!c) return HZ_EINVAL;
   if (n_frames < 0) return fail(c, HZ_EINVAL, "n_frames < 0");
+  if (n_frames == 0) return HZ_OK;  // nothing to do (the buffers may be empty)
   if (flags & ~uint32_t(HZ_IO_HOST | HZ_INPUT_NV12)) return fail(c, HZ_EINVAL, "unknown flags");
   const bool nv12 = (flags & HZ_INPUT_NV12) != 0;
   HZ_TRY(check_frame(c, in, W, H, in_pitch, out, out_pitch, true, true, nv12));

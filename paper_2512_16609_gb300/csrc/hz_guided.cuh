@@ -87,10 +87,11 @@ __device__ __forceinline__ void gf_quant(const GfArgs& g, int y, int x, float (&
 // Vertical window sums, thread per column, GF_VBAND output rows per block.
 // Rows are read GF_VU at a time (all loads issued before the sums use them)
 // so that each thread keeps several rows in flight.
-template <int PASS>
-__global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
-  constexpr int NQ = (PASS == 1) ? 4 : 2;
+template <int PASS, int KQ>
+__device__ __forceinline__ void gf_v_body(const GfArgs& g) {
+  constexpr int NQ = 2;  // quantities KQ, KQ + 1 of pass PASS
   constexpr int U = GF_VU;
+  constexpr int kq = KQ;
   const int x = blockIdx.x * GF_VCOLS + threadIdx.x;
   const int y0 = blockIdx.y * GF_VBAND;
   if (x >= g.W || y0 >= g.H) return;
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
     for (int u = 0; u < U; ++u)
       if (y + u <= yb) {
 #pragma unroll
-        for (int k = 0; k < NQ; ++k) s[k].add(q[u][k]);
+        for (int k = 0; k < NQ; ++k) s[k].add(q[u][kq + k]);
       }
   }
   const long long plane = (long long)g.W * g.H;
@@ -129,12 +130,20 @@ __global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
       if (y + u >= y1) break;
 #pragma unroll
       for (int k = 0; k < NQ; ++k) {
-        g.vs[k * plane + (long long)(y + u) * g.W + x] = s[k].get();
-        s[k].add(qi[u][k]);
-        s[k].add(-qo[u][k]);
+        g.vs[(kq + k) * plane + (long long)(y + u) * g.W + x] = s[k].get();
+        s[k].add(qi[u][kq + k]);
+        s[k].add(-qo[u][kq + k]);
       }
     }
   }
+}
+
+// Pass 1 runs its four sums as two pairs (blockIdx.z), halving the state a
+// thread carries.
+template <int PASS>
+__global__ void __launch_bounds__(GF_VCOLS) k_gf_v(const GfArgs g) {
+  if (PASS == 2 || blockIdx.z == 0) gf_v_body<PASS, 0>(g);
+  else gf_v_body<PASS, 2>(g);
 }
 
 // Horizontal window sums of the vertical sums for GF_HSEG outputs of one

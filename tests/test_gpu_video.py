@@ -388,3 +388,62 @@ def test_adaptive_gamma_sequence_and_image_mode():
     assert abs(info.gamma - ref.extra["gamma"]) <= 1e-4 * ref.extra["gamma"]
     mx, _ = u8_diff(o, ref.out)
     assert mx <= 1
+
+
+def test_full_size_pipelined_waves_sampled_against_oracle():
+    """The benchmark's launch configuration at its frame size: 64 frames of
+    1920x1080 in waves of 256 MiB (two waves through the three-stream
+    pipeline) with graph replay, no smoothing so that every frame stands
+    alone; sampled frames (the first and last of each wave) against the
+    oracle, and every frame against its own single-frame call."""
+    W, H = 1920, 1080
+    base = [hazegen.make_frame(W, H, seed=70 + k, beta=0.8 + 0.2 * k) for k in range(4)]
+    frames = np.stack([base[f % 4] for f in range(64)])
+    with context() as (m, ctx):
+        m.hz_set_wave_bytes(ctx, 256 << 20)
+        m.hz_set_graph_replay(ctx, True)
+        inp = torch.from_numpy(frames).cuda()
+        out = torch.empty_like(inp)
+        for _ in range(4):  # direct (sizing the scratch), direct, captured, replayed
+            m.hz_dehaze_video(ctx, inp, out)
+        torch.cuda.synchronize()
+        caps, reps = m.hz_get_graph_stats(ctx)
+        assert caps >= 1 and reps >= 1
+        infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
+        o = out.cpu().numpy()
+        for f in (0, 3, 42, 43, 63):
+            single, _ = empty_dev(W, H)
+            m.hz_dehaze_frame(ctx, inp[f], single)
+            np.testing.assert_array_equal(single.cpu().numpy(), o[f])
+    for f in (0, 43, 63):
+        ref = O.dehaze_frame(frames[f], oracle_params())
+        assert infos[f].T == ref.T and infos[f].cut_index == ref.cut_index
+        assert list(infos[f].S) == [int(v) for v in ref.S]
+        mx, exact = u8_diff(o[f], ref.out)
+        assert mx <= 1 and exact > 0.995
+
+
+@pytest.mark.parametrize("W,H", [(16384, 40), (24, 16384)])
+def test_maximum_dimensions(W, H):
+    I = hazegen.random_u8_image(W, H, 5, levels=64) + 96
+    with context(patch=7) as (m, ctx):
+        It = to_dev(I)
+        D = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        m.hz_dark_channel(ctx, It, D)
+        out, _ = empty_dev(W, H)
+        info = m.hz_dehaze_frame(ctx, It, out, want_info=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(D.cpu().numpy(), O.dark_channel(I, 7))
+        ref = O.dehaze_frame(I, oracle_params(patch=7))
+        assert info.T == ref.T and info.cut_index == ref.cut_index
+        assert u8_diff(out.cpu().numpy(), ref.out)[0] <= 1
+        with pytest.raises(m.HzError):  # one past the largest dimension
+            big = torch.zeros((1, 16385, 3), dtype=torch.uint8, device="cuda")
+            m.hz_dehaze_frame(ctx, big, torch.zeros_like(big))
+
+
+def test_empty_calls():
+    with context() as (m, ctx):
+        z = torch.zeros((0, 32, 32, 3), dtype=torch.uint8, device="cuda")
+        assert m.hz_dehaze_video(ctx, z, torch.zeros_like(z)) is None
+        assert m.hz_dehaze_batch(ctx, [], []) is None
