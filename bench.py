@@ -272,8 +272,9 @@ def run_variants(hzp, dev, frames_np, reps=10):
             out[name] = {"ms_per_step": ms, "frames_per_s": n / (ms / 1e3)}
         finally:
             hzp.hz_destroy(ctx)
-    nv = np.stack([hazegen.rgb_to_nv12(frames_np[f]) for f in range(30)])
-    nv_dev = torch.from_numpy(np.concatenate([nv] * (n // 30 + 1))[:n]).to(dev)
+    k = min(30, n)
+    nv = np.stack([hazegen.rgb_to_nv12(frames_np[f]) for f in range(k)])
+    nv_dev = torch.from_numpy(np.concatenate([nv] * (n // k + 1))[:n]).to(dev)
     ctx = hzp.hz_create(hzp.params(airlight_ema=0.9), dev.index)
     try:
         hzp.hz_set_wave_bytes(ctx, 256 << 20)
