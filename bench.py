@@ -574,6 +574,18 @@ def arrivals(seconds, seed=7):
     return ev
 
 
+def _lat_by_res(by_res):
+    out = {}
+    for r, lat in by_res.items():
+        if not lat:
+            continue
+        W_, H_, _, g = SERVED_MIX[r]
+        a = np.sort(np.asarray(lat))
+        out[f"{W_}x{H_}{' guided' if g else ''}"] = {
+            "frames": int(a.size), "p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99))}
+    return out
+
+
 def run_served(hzp, dev, frames_by_res, seconds):
     """Served streams through hz_submit/hz_poll vs the plain per-frame path,
     same arrivals; host (pinned) input and output buffers."""
@@ -603,12 +615,15 @@ def run_served(hzp, dev, frames_by_res, seconds):
         r = kinds[k][0]
         tickets.append(hzp.hz_submit(ctx, sids[k], host_in[r][counts[k] % SERVED_FRAMES], outs[k], hzp.HZ_IO_HOST))
         counts[k] += 1
-    for t in tickets:
-        hzp.hz_poll(ctx, t, -1)
+    by_res = {r: [] for r in range(len(SERVED_MIX))}
+    for (ta, k), t in zip(ev, tickets):
+        _, info = hzp.hz_poll(ctx, t, -1)
+        by_res[kinds[k][0]].append(info.latency_ms)
     wall = time.perf_counter() - t0
     st = hzp.hz_get_server_stats(ctx)
     served = {"frames": int(st.frames_done), "batches": int(st.batches), "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-              "mean_ms": st.mean_ms, "max_ms": st.max_ms, "frames_per_s": st.frames_done / wall}
+              "mean_ms": st.mean_ms, "max_ms": st.max_ms, "frames_per_s": st.frames_done / wall,
+              "by_resolution": _lat_by_res(by_res)}
     hzp.hz_destroy(ctx)
     # ---- plain per-frame path: FIFO, one call per frame, host copies ----
     ctx = hzp.hz_create(prm, dev.index or 0)
@@ -617,6 +632,7 @@ def run_served(hzp, dev, frames_by_res, seconds):
             for r in range(len(SERVED_MIX))}
     stream = torch.cuda.current_stream(dev)
     lat = []
+    plain_by_res = {r: [] for r in range(len(SERVED_MIX))}
     counts = [0] * len(kinds)
     t0 = time.perf_counter()
     for (ta, k) in ev:
@@ -634,12 +650,13 @@ def run_served(hzp, dev, frames_by_res, seconds):
         stream.synchronize()
         counts[k] += 1
         lat.append(1e3 * (time.perf_counter() - t0 - ta))
+        plain_by_res[r].append(lat[-1])
     wall = time.perf_counter() - t0
     hzp.hz_destroy(ctx)
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
     plain = {"frames": len(lat), "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": sum(lat) / len(lat),
-             "max_ms": lat[-1], "frames_per_s": len(lat) / wall}
+             "max_ms": lat[-1], "frames_per_s": len(lat) / wall, "by_resolution": _lat_by_res(plain_by_res)}
     return {"workload": "32 streams: 12x1280x720 + 12x1920x1080 video, 8x3840x2160 guided FP16 (r 60), "
                         f"Poisson {SERVED_FPS:.0f} fps each, {seconds:.0f} s, pinned host I/O",
             "served": served, "plain_fifo": plain}

@@ -137,6 +137,8 @@ typedef struct hz_frame_info {
   float mean_jg[3];    /* channel means of J_gamma (0 when balance is off) */
   float gamma;         /* exponent of Eq. 8 used for this frame */
   float mean_luma;     /* mean BT.601 luminance of J (adaptive gamma; else 0) */
+  float latency_ms;    /* hz_poll: time from hz_submit to the frame's completion
+                          (outputs copied back); 0 for the other calls */
 } hz_frame_info;
 
 /* One frame of a mixed-size batch (hz_dehaze_batch). */

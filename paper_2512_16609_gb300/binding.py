@@ -59,6 +59,7 @@ class hz_frame_info(C.Structure):
         ("mean_jg", C.c_float * 3),
         ("gamma", C.c_float),
         ("mean_luma", C.c_float),
+        ("latency_ms", C.c_float),
     ]
 
     def as_dict(self):
@@ -66,7 +67,7 @@ class hz_frame_info(C.Structure):
             "A": list(self.A), "A_hat": list(self.A_hat), "K": self.K, "n_above": self.n_above,
             "cut_index": self.cut_index, "S": list(self.S), "T": self.T, "status": self.status,
             "gains": list(self.gains), "mean_jg": list(self.mean_jg),
-            "gamma": self.gamma, "mean_luma": self.mean_luma,
+            "gamma": self.gamma, "mean_luma": self.mean_luma, "latency_ms": self.latency_ms,
         }
 
 

@@ -99,6 +99,7 @@ static void complete_loop(Server* S) {
         const Request& r = sl.reqs[i];
         hz_status fs = st;
         if (fs == HZ_OK && infos[i].status != 0) fs = HZ_EDEVICE_TIMEOUT;
+        infos[i].latency_ms = float(1e3 * (t - r.t_submit));
         S->done[r.ticket] = DoneRec{fs, infos[i]};
         S->lat_ms.push_back(1e3 * (t - r.t_submit));
         if (S->outstanding[r.sid]) --S->outstanding[r.sid];
