@@ -270,6 +270,10 @@ struct P1S {
   static constexpr int NHIST = 4;                               // histogram copies (warps share)
   static constexpr int OFF_MBAR = OFF_HIST + NHIST * 256 * 4;
   static constexpr int SMEM = OFF_MBAR + NCH * 8 + 16;
+  // registers per thread: up to R = 7, three blocks (3 x 288 x 64) leave
+  // room on the SM for a reconstruction block of 256 x 40 from another
+  // stream; larger windows keep what their vHGW state needs
+  static constexpr int MAXNREG = (R <= 7) ? 64 : 128;
 };
 
 // staged copies (S0 + 3 EW + 15) and item chunk reads stay inside a slot
@@ -620,7 +624,7 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
 }
 
 template <int R>
-__global__ void __launch_bounds__(P1S<R>::NT) k_p1(const __grid_constant__ HzJobs jobs) {
+__global__ void __maxnreg__(P1S<R>::MAXNREG) k_p1(const __grid_constant__ HzJobs jobs) {
   extern __shared__ __align__(128) unsigned char smem[];
   const HzJob& jb = jobs.j[blockIdx.y];
   const int item = blockIdx.x;
@@ -1216,9 +1220,10 @@ __device__ __forceinline__ void p3_unit(const HzJob& jb, const HzKParams& kp, in
   }
 }
 
-
+// At most 40 registers (six blocks per SM): one block fits beside three
+// dark-channel blocks of the next wave, which run on another stream.
 template <int MODE>
-__global__ void __launch_bounds__(P3_THREADS, 5) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
+__global__ void __launch_bounds__(P3_THREADS, 6) k_p3(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   const HzJob& jb = jobs.j[blockIdx.y];
   if ((int)blockIdx.x >= p3_units(jb.W, jb.H)) return;
   p3_unit<MODE>(jb, kp, blockIdx.x);
