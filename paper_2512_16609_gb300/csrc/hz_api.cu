@@ -53,13 +53,18 @@ static cudaError_t set_attr_one() {
   return cudaFuncSetAttribute(k_p1<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, P1S<R>::SMEM);
 }
 
-hz_status set_p1_attributes(hz_ctx* c) {
+hz_status set_kernel_attributes(hz_ctx* c) {
   HZ_CK(c, set_attr_one<0>());  HZ_CK(c, set_attr_one<1>());  HZ_CK(c, set_attr_one<2>());
   HZ_CK(c, set_attr_one<3>());  HZ_CK(c, set_attr_one<4>());  HZ_CK(c, set_attr_one<5>());
   HZ_CK(c, set_attr_one<6>());  HZ_CK(c, set_attr_one<7>());  HZ_CK(c, set_attr_one<8>());
   HZ_CK(c, set_attr_one<9>());  HZ_CK(c, set_attr_one<10>()); HZ_CK(c, set_attr_one<11>());
   HZ_CK(c, set_attr_one<12>()); HZ_CK(c, set_attr_one<13>()); HZ_CK(c, set_attr_one<14>());
   HZ_CK(c, set_attr_one<15>());
+  // the resize kernel: one source buffer fits at the largest frame sizes,
+  // two wherever they fit in the per-block limit
+  static_assert(rs_smem(HZ_MAX_DIM, HZ_MAX_DIM, 0, 1) <= RS_SMEM_LIMIT, "resize staging");
+  static_assert(rs_smem(HZ_MAX_DIM, HZ_MAX_DIM, 1, 1) <= RS_SMEM_LIMIT, "resize staging");
+  HZ_CK(c, cudaFuncSetAttribute(k_resize, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_LIMIT));
   return HZ_OK;
 }
 
@@ -145,7 +150,9 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
                          cudaStream_t s) {
   ResizeJobs rj, cj;  // resize (any format), NV12 conversion at the same size
   rj.n = cj.n = 0;
-  unsigned most = 0, most_c = 0;
+  rj.dbl = cj.dbl = 0;
+  unsigned most_rows = 0, most_c = 0;
+  int rs1 = 0, rs2 = 0;  // resize shared memory with one / two source buffers
   for (int i = 0; i < n; ++i) {
     const FramePlan& f = lp.fp[i];
     if (f.resized || f.nv12) {
@@ -162,7 +169,11 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
       r.dH = f.H;
       r.nv12 = f.nv12 ? 1 : 0;
       r.pad = 0;
-      if (!same) most = std::max(most, unsigned(f.W) * unsigned(f.H));
+      if (!same) {
+        most_rows = std::max(most_rows, unsigned((f.H + RS_ROWS - 1) / RS_ROWS));
+        rs1 = std::max(rs1, rs_smem(f.in_W, f.W, r.nv12, 1));
+        rs2 = std::max(rs2, rs_smem(f.in_W, f.W, r.nv12, 2));
+      }
     } else if (f.off_copy) {
       HZ_CK(c, cudaMemcpy2DAsync(base + f.off_copy, size_t(f.copy_pitch), fr[i].in, fr[i].in_pitch,
                                  size_t(3) * f.W, size_t(f.H), cudaMemcpyDeviceToDevice, s));
@@ -170,7 +181,8 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
   }
   if (rj.n) {
     LaunchScope ls(c, HZ_K_RESIZE, s);
-    k_resize<<<dim3((most + 255) / 256, rj.n), 256, 0, s>>>(rj);
+    rj.dbl = rs2 <= RS_SMEM_LIMIT ? 1 : 0;
+    k_resize<<<dim3(most_rows, rj.n), RS_THREADS, rj.dbl ? rs2 : rs1, s>>>(rj);
     HZ_CK(c, cudaGetLastError());
   }
   if (cj.n) {
@@ -472,7 +484,7 @@ extern "C" hz_status hz_create(const hz_params* p, int device, size_t mem_budget
     ok = cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_out[i], cudaEventDisableTiming) == cudaSuccess;
-  if (ok) ok = set_p1_attributes(c) == HZ_OK;
+  if (ok) ok = set_kernel_attributes(c) == HZ_OK;
   if (!ok) {
     cudaGetLastError();
     hz_destroy(c);
@@ -1022,9 +1034,10 @@ extern "C" hz_status hz_resize(hz_ctx* c, const uint8_t* in, int32_t W, int32_t 
   ResizeJobs rj;
   rj.n = 1;
   rj.j[0] = ResizeJob{in, (long long)in_pitch, out, (long long)out_pitch, W, H, W2, H2, 0, 0};
+  rj.dbl = rs_smem(W, W2, 0, 2) <= RS_SMEM_LIMIT ? 1 : 0;
   {
     LaunchScope ls(c, HZ_K_RESIZE, s);
-    k_resize<<<dim3(unsigned((size_t(W2) * H2 + 255) / 256), 1), 256, 0, s>>>(rj);
+    k_resize<<<dim3(unsigned((H2 + RS_ROWS - 1) / RS_ROWS), 1), RS_THREADS, rs_smem(W, W2, 0, rj.dbl ? 2 : 1), s>>>(rj);
   }
   HZ_CK(c, cudaGetLastError());
   return mark_done(c, s);

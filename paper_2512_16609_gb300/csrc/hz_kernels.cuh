@@ -95,7 +95,7 @@ struct ResizeJob {
 };
 struct ResizeJobs {
   int n;
-  int pad;
+  int dbl;  // k_resize: two source-row buffers (next row's copies in flight)
   ResizeJob j[MAXJ];
 };
 
@@ -112,25 +112,18 @@ __device__ __forceinline__ void resize_taps(int i, int n_in, int n_out, int& i0,
   i1 = min(i0 + 1, n_in - 1);
 }
 
-// RGB of source pixel (x, y). NV12: BT.601 limited range with the 8-bit
-// integer coefficients, C = Y - 16, D = Cb - 128, E = Cr - 128,
-// R = (298 C + 409 E + 128) >> 8, G = (298 C - 100 D - 208 E + 128) >> 8,
-// B = (298 C + 516 D + 128) >> 8 (arithmetic shifts), clipped to [0, 255];
-// the chroma sample of (x, y) is (x / 2, y / 2).
-__device__ __forceinline__ void src_rgb(const ResizeJob& r, int x, int y, int (&v)[3]) {
-  if (r.nv12) {
-    const int C = int(__ldg(r.src + (long long)y * r.src_pitch + x)) - 16;
-    const uint8_t* uv = r.src + (long long)(r.sH + (y >> 1)) * r.src_pitch + 2 * (x >> 1);
-    const int D = int(__ldg(uv)) - 128, E = int(__ldg(uv + 1)) - 128;
-    v[0] = min(max((298 * C + 409 * E + 128) >> 8, 0), 255);
-    v[1] = min(max((298 * C - 100 * D - 208 * E + 128) >> 8, 0), 255);
-    v[2] = min(max((298 * C + 516 * D + 128) >> 8, 0), 255);
-  } else {
-    const uint8_t* p = r.src + (long long)y * r.src_pitch + 3LL * x;
-    v[0] = __ldg(p);
-    v[1] = __ldg(p + 1);
-    v[2] = __ldg(p + 2);
-  }
+// RGB of pixel x from staged NV12 rows (a luma row and its chroma row):
+// BT.601 limited range with the 8-bit integer coefficients, C = Y - 16,
+// D = Cb - 128, E = Cr - 128, R = (298 C + 409 E + 128) >> 8,
+// G = (298 C - 100 D - 208 E + 128) >> 8, B = (298 C + 516 D + 128) >> 8
+// (arithmetic shifts), clipped to [0, 255]; the chroma sample of (x, y) is
+// (x / 2, y / 2).
+__device__ __forceinline__ void staged_nv12(const uint8_t* luma, const uint8_t* chroma, int x, int (&v)[3]) {
+  const int C = int(luma[x]) - 16;
+  const int D = int(chroma[2 * (x >> 1)]) - 128, E = int(chroma[2 * (x >> 1) + 1]) - 128;
+  v[0] = min(max((298 * C + 409 * E + 128) >> 8, 0), 255);
+  v[1] = min(max((298 * C - 100 * D - 208 * E + 128) >> 8, 0), 255);
+  v[2] = min(max((298 * C + 516 * D + 128) >> 8, 0), 255);
 }
 
 // NV12 to RGB at the same size, 16 pixels of a row per thread: 16 luma
@@ -196,27 +189,148 @@ __global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ Resize
   }
 }
 
-// Input preparation: NV12 conversion and/or resize into the plan buffer.
-__global__ void __launch_bounds__(256) k_resize(const __grid_constant__ ResizeJobs jobs) {
-  const ResizeJob& r = jobs.j[blockIdx.y];
-  const unsigned i = blockIdx.x * 256u + threadIdx.x;
-  if (i >= unsigned(r.dW) * unsigned(r.dH)) return;
-  const int y = int(i / unsigned(r.dW)), x = int(i - unsigned(y) * unsigned(r.dW));
-  int x0, x1, wx, y0, y1, wy;
-  resize_taps(x, r.sW, r.dW, x0, x1, wx);
+// Input preparation: resize (any source format) into the plan buffer,
+// RS_ROWS output rows per block. The block first tabulates the horizontal
+// taps of its frame in shared memory (x0 in bits 0-13, x1 - x0 in bit 14,
+// the weight of x1 in bits 15-23). Per output row it then copies the source
+// rows its taps read (two rows; for NV12 their two luma rows and two chroma
+// rows) into shared memory with asynchronous 16-byte copies of the aligned
+// chunks that cover them, each row keeping its address modulo 16 (a chunk
+// that holds a byte of the row lies in that byte's page); with two buffers
+// (jobs.dbl) the next row's copies are in flight while the current row is
+// formed. Outputs go to a shared output row, which is written out in 16-byte
+// stores when its destination is aligned.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROWS = 4;                // output rows per block
+constexpr int RS_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory per block
+// staged bytes of one source row of `bytes` bytes (alignment slack included)
+__host__ __device__ constexpr int rs_row_slot(int bytes) { return (bytes + 15 + 15) & ~15; }
+// one buffer of staged source rows
+__host__ __device__ constexpr int rs_src_bytes(int sW, int nv12) {
+  return nv12 ? 4 * rs_row_slot(sW) : 2 * rs_row_slot(3 * sW);
+}
+// dynamic shared memory of a job: tap table, nbuf source buffers, output row
+__host__ __device__ constexpr int rs_smem(int sW, int dW, int nv12, int nbuf) {
+  return ((4 * dW + 15) & ~15) + nbuf * rs_src_bytes(sW, nv12) + ((3 * dW + 15) & ~15);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(unsigned(__cvta_generic_to_shared(dst_smem))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Starts the copy of `bytes` bytes at src into the 16-byte aligned slot dst;
+// returns the slot offset of byte 0 (src modulo 16).
+__device__ __forceinline__ int rs_stage_row(uint8_t* dst, const uint8_t* src, int bytes) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+  const uintptr_t a1 = (reinterpret_cast<uintptr_t>(src) + uintptr_t(bytes) + 15) & ~uintptr_t(15);
+  const int nch = int((a1 - a0) >> 4);
+  for (int k = threadIdx.x; k < nch; k += RS_THREADS) cp_async16(dst + 16 * k, reinterpret_cast<const void*>(a0 + 16 * k));
+  return int(reinterpret_cast<uintptr_t>(src) & 15);
+}
+
+// Source rows of output row y in buffer `buf`: slot offsets of the rows.
+struct RsRows {
+  const uint8_t *row0, *row1, *ch0, *ch1;
+};
+__device__ __forceinline__ RsRows rs_stage(const ResizeJob& r, int y, uint8_t* buf) {
+  int y0, y1, wy;
   resize_taps(y, r.sH, r.dH, y0, y1, wy);
-  int p00[3], p01[3], p10[3], p11[3];
-  src_rgb(r, x0, y0, p00);
-  src_rgb(r, x1, y0, p01);
-  src_rgb(r, x0, y1, p10);
-  src_rgb(r, x1, y1, p11);
-  uint8_t* o = r.dst + (long long)y * r.dst_pitch + 3LL * x;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int top = (256 - wx) * p00[c] + wx * p01[c];
-    const int bot = (256 - wx) * p10[c] + wx * p11[c];
-    o[c] = uint8_t(((256 - wy) * top + wy * bot + (1 << 15)) >> 16);
+  RsRows q;
+  if (r.nv12) {
+    const int ls = rs_row_slot(r.sW);
+    const uint8_t* cbase = r.src + (long long)r.sH * r.src_pitch;
+    q.row0 = buf + rs_stage_row(buf, r.src + (long long)y0 * r.src_pitch, r.sW);
+    q.row1 = buf + ls + rs_stage_row(buf + ls, r.src + (long long)y1 * r.src_pitch, r.sW);
+    q.ch0 = buf + 2 * ls + rs_stage_row(buf + 2 * ls, cbase + (long long)(y0 >> 1) * r.src_pitch, r.sW);
+    q.ch1 = buf + 3 * ls + rs_stage_row(buf + 3 * ls, cbase + (long long)(y1 >> 1) * r.src_pitch, r.sW);
+  } else {
+    const int rs = rs_row_slot(3 * r.sW);
+    q.row0 = buf + rs_stage_row(buf, r.src + (long long)y0 * r.src_pitch, 3 * r.sW);
+    q.row1 = buf + rs + rs_stage_row(buf + rs, r.src + (long long)y1 * r.src_pitch, 3 * r.sW);
+    q.ch0 = q.ch1 = nullptr;
   }
+  return q;
+}
+
+__device__ __forceinline__ int rs_lerp(int p00, int p01, int p10, int p11, int wx, int wy) {
+  const int top = (256 - wx) * p00 + wx * p01;
+  const int bot = (256 - wx) * p10 + wx * p11;
+  return ((256 - wy) * top + wy * bot + (1 << 15)) >> 16;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_resize(const __grid_constant__ ResizeJobs jobs) {
+  extern __shared__ __align__(16) uint8_t rs_smem_buf[];
+  const ResizeJob& r = jobs.j[blockIdx.y];
+  const int yb = blockIdx.x * RS_ROWS;
+  if (yb >= r.dH) return;
+  const bool dbl = jobs.dbl != 0;
+  uint32_t* tap = reinterpret_cast<uint32_t*>(rs_smem_buf);
+  uint8_t* src0 = rs_smem_buf + ((4 * r.dW + 15) & ~15);
+  const int sb = rs_src_bytes(r.sW, r.nv12);
+  uint8_t* orow = src0 + (dbl ? 2 : 1) * sb;
+  for (int x = threadIdx.x; x < r.dW; x += RS_THREADS) {
+    int x0, x1, wx;
+    resize_taps(x, r.sW, r.dW, x0, x1, wx);
+    tap[x] = uint32_t(x0) | (uint32_t(x1 - x0) << 14) | (uint32_t(wx) << 15);
+  }
+  const int ye = min(yb + RS_ROWS, r.dH);
+  RsRows cur = rs_stage(r, yb, src0);
+  cp_async_commit();
+  for (int y = yb; y < ye; ++y) {
+    RsRows nxt = cur;
+    if (dbl) {
+      // the next row's copies go to the other buffer, freed after row y - 1
+      if (y + 1 < ye) nxt = rs_stage(r, y + 1, src0 + ((y + 1 - yb) & 1) * sb);
+      cp_async_commit();
+      cp_async_wait<1>();  // this thread's copies of row y have landed
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // every thread's copies of row y (and the tap table) visible; row y - 1 is out
+    int y0, y1, wy;
+    resize_taps(y, r.sH, r.dH, y0, y1, wy);
+    for (int x = threadIdx.x; x < r.dW; x += RS_THREADS) {
+      const uint32_t t = tap[x];
+      const int x0 = int(t & 0x3fffu), x1 = x0 + int((t >> 14) & 1u), wx = int(t >> 15);
+      uint8_t* o = orow + 3 * x;
+      if (r.nv12) {
+        int p00[3], p01[3], p10[3], p11[3];
+        staged_nv12(cur.row0, cur.ch0, x0, p00);
+        staged_nv12(cur.row0, cur.ch0, x1, p01);
+        staged_nv12(cur.row1, cur.ch1, x0, p10);
+        staged_nv12(cur.row1, cur.ch1, x1, p11);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c] = uint8_t(rs_lerp(p00[c], p01[c], p10[c], p11[c], wx, wy));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          o[c] = uint8_t(rs_lerp(cur.row0[3 * x0 + c], cur.row0[3 * x1 + c], cur.row1[3 * x0 + c],
+                                 cur.row1[3 * x1 + c], wx, wy));
+      }
+    }
+    __syncthreads();  // output row complete; the buffer of row y is free
+    if (!dbl && y + 1 < ye) {
+      nxt = rs_stage(r, y + 1, src0);
+      cp_async_commit();
+    }
+    uint8_t* og = r.dst + (long long)y * r.dst_pitch;
+    const int ob = 3 * r.dW;
+    if ((reinterpret_cast<uintptr_t>(og) & 15) == 0) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(orow);
+      uint4* o4 = reinterpret_cast<uint4*>(og);
+      for (int k = threadIdx.x; k < (ob >> 4); k += RS_THREADS) o4[k] = s4[k];
+      for (int i = (ob & ~15) + threadIdx.x; i < ob; i += RS_THREADS) og[i] = orow[i];
+    } else {
+      for (int i = threadIdx.x; i < ob; i += RS_THREADS) og[i] = orow[i];
+    }
+    cur = nxt;
+  }
+  cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------------

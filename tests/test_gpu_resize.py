@@ -11,8 +11,11 @@ from tests.gpu_util import context, empty_dev, oracle_params, to_dev, torch, u8_
 
 pytestmark = pytest.mark.gpu
 
+# the last two are wider than two staged source rows per block allow (one
+# buffer, copies not overlapped with the arithmetic)
 CASES = [(1280, 720, 640, 480), (1920, 1080, 640, 480), (1000, 700, 640, 480), (333, 251, 640, 480),
-         (97, 61, 40, 31), (64, 48, 64, 48), (640, 480, 1, 1), (5, 3, 17, 9)]
+         (97, 61, 40, 31), (64, 48, 64, 48), (640, 480, 1, 1), (5, 3, 17, 9),
+         (16384, 5, 13001, 3), (12000, 6, 16384, 7)]
 
 
 @pytest.mark.parametrize("W,H,W2,H2", CASES)
