@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ Resize
 // formed. Outputs go to a shared output row, which is written out in 16-byte
 // stores when its destination is aligned.
 constexpr int RS_THREADS = 256;
-constexpr int RS_ROWS = 4;                // output rows per block
+constexpr int RS_ROWS = 8;                // output rows per block
 constexpr int RS_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory per block
 // staged bytes of one source row of `bytes` bytes (alignment slack included)
 __host__ __device__ constexpr int rs_row_slot(int bytes) { return (bytes + 15 + 15) & ~15; }
