@@ -19,6 +19,7 @@ HZ_T_DCP, HZ_T_FAST = 0, 1
 HZ_PREC_FP32, HZ_PREC_FP16 = 0, 1
 HZ_MAX_PATCH, HZ_MAX_GF_RADIUS, HZ_MAX_DIM = 31, 255, 16384
 HZ_IO_HOST, HZ_GUIDED, HZ_INPUT_NV12 = 0x1, 0x2, 0x4
+HZ_INJECT_WITHHOLD_ROW_COPIES = 0x1
 HZ_STREAM_STATE_BYTES = 48
 
 
@@ -153,6 +154,7 @@ _SIGS = {
     "hz_resize": (C.c_int, [_P, _P, _I, _I, _SZ, _P, _I, _I, _SZ, _P]),
     "hz_autotune_wave_bytes": (C.c_int, [_P, _P, _I, _P, C.POINTER(_SZ), C.POINTER(C.c_float), _I]),
     "hz_set_graph_replay": (C.c_int, [_P, C.c_int]),
+    "hz_set_fault_injection": (C.c_int, [_P, C.c_uint32]),
     "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "hz_get_wave_bytes": (C.c_int, [_P, C.POINTER(_SZ)]),
     "hz_get_profile": (C.c_int, [_P, C.POINTER(hz_profile), C.c_int]),
@@ -493,6 +495,13 @@ def hz_autotune_wave_bytes(ctx, frames, outs, stream_ids=None, guided=None, stre
 
 def hz_set_graph_replay(ctx, on: bool):
     return _check(lib().hz_set_graph_replay(ctx, 1 if on else 0), ctx, "hz_set_graph_replay")
+
+
+def hz_set_fault_injection(ctx, mask: int):
+    """Failure-detection test hook: HZ_INJECT_WITHHOLD_ROW_COPIES makes the
+    dark-channel kernel's bounded wait run out (frames report
+    HZ_EDEVICE_TIMEOUT); 0 restores normal operation."""
+    return _check(lib().hz_set_fault_injection(ctx, int(mask)), ctx, "hz_set_fault_injection")
 
 
 def hz_get_graph_stats(ctx):

@@ -98,6 +98,7 @@ hz_status mark_done(hz_ctx* c, cudaStream_t s) {
 void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video,
                uint8_t* base) {
   jobs.n = n;
+  jobs.inject = int(c->inject);
   uint8_t* A = base ? base : c->arena.base;
   for (int i = 0; i < n; ++i) {
     const FramePlan& f = lp.fp[i];
@@ -338,6 +339,9 @@ hz_status read_infos(hz_ctx* c, const LaunchPlan& lp, int n, cudaStream_t s, hz_
   HZ_CK(c, cudaMemcpyAsync(c->rec_host, c->arena.base, sizeof(HzFrameRec) * size_t(n), cudaMemcpyDeviceToHost, s));
   HZ_CK(c, cudaStreamSynchronize(s));
   recs_to_infos(c->rec_host, lp, n, infos, balance);
+  for (int i = 0; i < n; ++i)
+    if (infos[i].status == HZ_EDEVICE_TIMEOUT)
+      return fail(c, HZ_EDEVICE_TIMEOUT, "frame %d: a bounded device-side wait gave up", i);
   return HZ_OK;
 }
 
@@ -734,6 +738,7 @@ static std::string call_key(const hz_ctx* c, const void* a, size_t na, const voi
   const uintptr_t bases[2] = {uintptr_t(c->arena.base), uintptr_t(c->stage.base)};
   k.append(reinterpret_cast<const char*>(&c->prm), sizeof c->prm);
   k.append(reinterpret_cast<const char*>(&c->wave_bytes), sizeof c->wave_bytes);
+  k.append(reinterpret_cast<const char*>(&c->inject), sizeof c->inject);
   k.append(reinterpret_cast<const char*>(bases), sizeof bases);
   k.append(static_cast<const char*>(a), na);
   if (b) k.append(static_cast<const char*>(b), nb);
@@ -1284,6 +1289,17 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   return mark_done(c, s);
 }
 
+static_assert(HZ_INJECT_WITHHOLD_ROW_COPIES == unsigned(HZ_INJ_WITHHOLD_ROWS), "injection mask");
+static_assert(HZ_STATUS_DEVICE_TIMEOUT == HZ_EDEVICE_TIMEOUT, "device timeout status");
+
+extern "C" hz_status hz_set_fault_injection(hz_ctx* c, uint32_t mask) {
+  if (!c) return HZ_EINVAL;
+  if (mask & ~uint32_t(HZ_INJECT_WITHHOLD_ROW_COPIES)) return fail(c, HZ_EINVAL, "unknown injection mask 0x%x", mask);
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->inject = mask;
+  return HZ_OK;
+}
+
 extern "C" hz_status hz_set_graph_replay(hz_ctx* c, int on) {
   if (!c) return HZ_EINVAL;
   std::lock_guard<std::mutex> lk(c->call_mu);
@@ -1442,6 +1458,7 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
 
   HzJobs jobs;
   jobs.n = 1;
+  jobs.inject = 0;
   HzJob& j = jobs.j[0];
   const FramePlan& f = lp.fp[0];
   j = HzJob{};

@@ -119,9 +119,13 @@ struct HzJob {
 };
 
 constexpr int MAXJ = 64;  // frames per launch (jobs travel as a kernel parameter)
+// Failure injection (host-set test hook, no GPU fault): the dark-channel
+// kernel withholds the row copies of the first chunk of every region, so
+// that its bounded wait runs out and the frames report a device timeout.
+constexpr int HZ_INJ_WITHHOLD_ROWS = 1;
 struct HzJobs {
   int n;
-  int pad;
+  int inject;  // HZ_INJ_* mask, 0 in normal operation
   HzJob j[MAXJ];
 };
 

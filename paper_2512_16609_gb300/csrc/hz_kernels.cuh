@@ -428,13 +428,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       : "memory");
 }
 
-// Bounded wait on a chunk's barrier: false when it gave up (the caller
-// records HZ_STATUS_DEVICE_TIMEOUT and abandons the region).
-constexpr unsigned MBAR_SPIN_LIMIT = 1u << 22;
+// Bounded wait on a chunk's barrier: false when it gave up after
+// MBAR_WAIT_NS of the global timer (the caller records
+// HZ_STATUS_DEVICE_TIMEOUT and abandons the region).
+constexpr unsigned long long MBAR_WAIT_NS = 1000000000ull;  // one second
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, unsigned parity) {
-  for (unsigned it = 0; it < MBAR_SPIN_LIMIT; ++it)
-    if (mbar_try_wait(b, parity)) return true;
-  return false;
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(b, parity))
+    if (global_ns() - t0 > MBAR_WAIT_NS) return false;
+  return true;
 }
 
 // Stage every row of the band. Rows outside the frame (or past the last
@@ -470,7 +478,7 @@ __device__ __forceinline__ void p1_fill_rows(const HzJob& jb, int ya, int nrows_
 
 template <int R>
 __device__ __forceinline__ void p1_issue_rows(const HzJob& jb, int ya, int nrows_need, int xs, int xa, int xb,
-                                              unsigned char* smem, uint64_t* mbar, int lane) {
+                                              unsigned char* smem, uint64_t* mbar, int lane, int inject) {
   using G = P1S<R>;
   constexpr int NR = G::NCH * G::CH;
   int k_lo, k_hi;
@@ -490,6 +498,7 @@ __device__ __forceinline__ void p1_issue_rows(const HzJob& jb, int ya, int nrows
       src = reinterpret_cast<const void*>(a0);
       dst = smem + k * G::SLOT + G::S0 + (long long)(a0 - base);
     }
+    if (c == 0 && (inject & HZ_INJ_WITHHOLD_ROWS)) continue;  // failure injection: chunk 0 never completes
     mbar_expect_tx_arrive(mbar + c, bytes);
     if (bytes) bulk_g2s(dst, src, bytes, mbar + c);
   }
@@ -619,7 +628,7 @@ __device__ __forceinline__ void p1_hitem(const uint4* vq, int sp0, int W, int nv
 }
 
 template <int R>
-__device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned char* smem) {
+__device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned char* smem, int inject) {
   using G = P1S<R>;
   constexpr int P = G::P;
   const int tid = threadIdx.x;
@@ -645,7 +654,7 @@ __device__ __forceinline__ bool p1_region(const HzJob& jb, int item, unsigned ch
   __syncthreads();  // chunk barriers initialised
   if (tid >= G::NTC) {
     // producer warp: the row copies, then on to the block's later barriers
-    p1_issue_rows<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar, tid - G::NTC);
+    p1_issue_rows<R>(jb, ya, nrows_need, xs, xa, xb, smem, mbar, tid - G::NTC, inject);
   } else {
     // compute warps: clear the histograms, fill the rows without frame data
     for (int i = tid; i < G::NHIST * 256; i += G::NTC) whist[i] = 0u;
@@ -743,7 +752,7 @@ __global__ void __maxnreg__(P1S<R>::MAXNREG) k_p1(const __grid_constant__ HzJobs
   const HzJob& jb = jobs.j[blockIdx.y];
   const int item = blockIdx.x;
   if (item >= jb.tiles_x * jb.tiles_y) return;
-  p1_region<R>(jb, item, smem);
+  p1_region<R>(jb, item, smem, jobs.inject);
 }
 
 // ------------------------------------------------------------------------
@@ -798,7 +807,7 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp, int T, unsigne
   const unsigned long long gs = block_sum(sg, shl);
   const unsigned long long bs = block_sum(sb, shl);
   if (!s_found) {  // tie counts inconsistent with the histogram: report, touch nothing
-    if (tid == 0) rec->status = HZ_STATUS_SELECT_FAILED;
+    if (tid == 0 && rec->status == 0) rec->status = HZ_STATUS_SELECT_FAILED;
     return;
   }
   const int ystar = s_row;
@@ -1022,7 +1031,7 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
     __threadfence();
     if (T >= 0) {
       p2_finalize(jb, kp, T, s_above);  // its record writes are thread 0's
-    } else if (tid == 0) {
+    } else if (tid == 0 && rec->status == 0) {
       rec->status = HZ_STATUS_SELECT_FAILED;  // fewer than K pixels counted
     }
   }

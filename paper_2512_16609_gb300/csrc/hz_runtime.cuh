@@ -65,6 +65,7 @@ struct hz_ctx {
     uint64_t last_use = 0;
   };
   bool graphs = false;
+  uint32_t inject = 0;        // failure-injection mask (hz_set_fault_injection)
   cudaStream_t gs = nullptr;
   std::vector<GraphEntry> gcache;           // at most GRAPH_CACHE entries, least recently used evicted
   uint64_t g_tick = 0, g_captures = 0, g_replays = 0;
