@@ -858,7 +858,7 @@ __device__ void p2_finalize(const HzJob& jb, const HzKParams& kp, int T, unsigne
 
 // Candidate region of the selection: pixels with D > T add to the frame's
 // r/g/b sums, ties (D == T) to per-row counts and sums.
-__device__ void p2_scan_region(const HzJob& jb, int item, int T) {
+__device__ __forceinline__ void p2_scan_region(const HzJob& jb, int item, int T) {
   __shared__ unsigned long long shl[32];
   constexpr int nw = 8;  // k_p2 block
   const int tid = threadIdx.x;
@@ -1016,9 +1016,24 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   }
   __syncthreads();
   const int T = s_T;
-  if (T >= 0)
-    for (int item = blockIdx.x; item < nitems; item += nb)
-      if ((int)jb.tilemax[item] >= T) p2_scan_region(jb, item, T);
+  if (T >= 0) {
+    // the block's regions (b, b + nb, ...) 256 at a time: every region
+    // maximum is loaded at once and the candidates listed in shared memory
+    __shared__ int s_cand[256];
+    __shared__ int s_nc;
+    const int nmine = (nitems - (int)blockIdx.x + nb - 1) / nb;
+    for (int base = 0; base < nmine; base += 256) {
+      if (tid == 0) s_nc = 0;
+      __syncthreads();
+      const int k = base + tid;
+      const int item = (int)blockIdx.x + k * nb;
+      if (k < nmine && (int)jb.tilemax[item] >= T) s_cand[atomicAdd(&s_nc, 1)] = item;
+      __syncthreads();
+      const int nc = s_nc;
+      for (int c = 0; c < nc; ++c) p2_scan_region(jb, s_cand[c], T);
+      __syncthreads();
+    }
+  }
   // counters: thread 0 releases the block's writes (ordered before it by
   // the barrier) with one fence, then counts the block
   __syncthreads();
