@@ -1225,7 +1225,7 @@ extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
 // the fastest. Every run starts from the stream states saved at entry, which
 // are restored at the end: the tuning leaves no trace beyond the outputs,
 // which equal those of one ordinary call.
-static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256};
+static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256, 384, 512};
 
 extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
                                             size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates) {
