@@ -390,17 +390,22 @@ def test_adaptive_gamma_sequence_and_image_mode():
     assert mx <= 1
 
 
-def test_full_size_pipelined_waves_sampled_against_oracle():
-    """The benchmark's launch configuration at its frame size: 64 frames of
-    1920x1080 in waves of 256 MiB (two waves through the three-stream
-    pipeline) with graph replay, no smoothing so that every frame stands
-    alone; sampled frames (the first and last of each wave) against the
-    oracle, and every frame against its own single-frame call."""
+@pytest.mark.parametrize("n,wave_mib", [(64, 256), (130, 512)])
+def test_full_size_pipelined_waves_sampled_against_oracle(n, wave_mib):
+    """The benchmark's launch configurations at its frame size: 1920x1080
+    frames in waves of 256 MiB (43 frames: waves of 43 + 21) or 512 MiB (a
+    launch takes at most 64 frames: 64 + 64 + 2) through the three-stream
+    pipeline, with graph replay, no smoothing so that every frame stands
+    alone; the first and last frame of every wave against the oracle, and
+    against its own single-frame call."""
     W, H = 1920, 1080
     base = [hazegen.make_frame(W, H, seed=70 + k, beta=0.8 + 0.2 * k) for k in range(4)]
-    frames = np.stack([base[f % 4] for f in range(64)])
+    frames = np.stack([base[f % 4] for f in range(n)])
+    per = min(64, (wave_mib << 20) // (3 * W * H))
+    firsts = list(range(0, n, per))
+    sampled = sorted(set(firsts + [min(f + per, n) - 1 for f in firsts]))
     with context() as (m, ctx):
-        m.hz_set_wave_bytes(ctx, 256 << 20)
+        m.hz_set_wave_bytes(ctx, wave_mib << 20)
         m.hz_set_graph_replay(ctx, True)
         inp = torch.from_numpy(frames).cuda()
         out = torch.empty_like(inp)
@@ -411,12 +416,15 @@ def test_full_size_pipelined_waves_sampled_against_oracle():
         assert caps >= 1 and reps >= 1
         infos = m.hz_dehaze_video(ctx, inp, out, want_info=True)
         o = out.cpu().numpy()
-        for f in (0, 3, 42, 43, 63):
+        for f in sampled:
             single, _ = empty_dev(W, H)
             m.hz_dehaze_frame(ctx, inp[f], single)
             np.testing.assert_array_equal(single.cpu().numpy(), o[f])
-    for f in (0, 43, 63):
-        ref = O.dehaze_frame(frames[f], oracle_params())
+    refs = {}
+    for f in sampled:
+        if f % 4 not in refs:
+            refs[f % 4] = O.dehaze_frame(frames[f], oracle_params())
+        ref = refs[f % 4]
         assert infos[f].T == ref.T and infos[f].cut_index == ref.cut_index
         assert list(infos[f].S) == [int(v) for v in ref.S]
         mx, exact = u8_diff(o[f], ref.out)
