@@ -159,7 +159,7 @@ hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* f
     if (f.resized || f.nv12) {
       const bool same = !f.resized;
       ResizeJob& r = same ? cj.j[cj.n++] : rj.j[rj.n++];
-      if (same) most_c = std::max(most_c, unsigned((f.W + 15) / 16) * unsigned(f.H));
+      if (same) most_c = std::max(most_c, unsigned((f.W + 15) / 16) * unsigned(f.H / 2));
       r.src = fr[i].in;
       r.src_pitch = (long long)fr[i].in_pitch;
       r.dst = base + f.off_copy;

@@ -126,50 +126,33 @@ __device__ __forceinline__ void staged_nv12(const uint8_t* luma, const uint8_t* 
   v[2] = min(max((298 * C + 516 * D + 128) >> 8, 0), 255);
 }
 
-// NV12 to RGB at the same size, 16 pixels of a row per thread: 16 luma
-// bytes and 8 Cb/Cr pairs in (16-byte loads when aligned), 48 RGB bytes out
-// (three 16-byte stores; the plan buffer's rows are 16-byte aligned).
-__device__ __forceinline__ uint32_t nv12_px(int Y, int D, int E) {
-  const int C = Y - 16;
-  const int R = min(max((298 * C + 409 * E + 128) >> 8, 0), 255);
-  const int G = min(max((298 * C - 100 * D - 208 * E + 128) >> 8, 0), 255);
-  const int B = min(max((298 * C + 516 * D + 128) >> 8, 0), 255);
+// NV12 to RGB at the same size, 16 pixels of two rows (2y, 2y + 1) per
+// thread: the rows' 16 luma bytes and their shared 8 Cb/Cr pairs in (16-byte
+// loads when aligned), the chroma terms 409 E + 128, -100 D - 208 E + 128 and
+// 516 D + 128 formed once per 2 x 2 block, 2 x 48 RGB bytes out (16-byte
+// stores; the plan buffer's rows are 16-byte aligned).
+__device__ __forceinline__ uint32_t nv12_px(int Y, int cr, int cg, int cb) {
+  const int C = 298 * (Y - 16);
+  const int R = min(max((C + cr) >> 8, 0), 255);
+  const int G = min(max((C + cg) >> 8, 0), 255);
+  const int B = min(max((C + cb) >> 8, 0), 255);
   return uint32_t(R) | (uint32_t(G) << 8) | (uint32_t(B) << 16);
 }
 
-__global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ ResizeJobs jobs) {
-  const ResizeJob& r = jobs.j[blockIdx.y];
-  const unsigned gpr = unsigned(r.sW + 15) / 16u;
-  const unsigned g = blockIdx.x * 256u + threadIdx.x;
-  if (g >= gpr * unsigned(r.sH)) return;
-  const int y = int(g / gpr), x = int(g - unsigned(y) * gpr) * 16;
-  const int nv = min(16, r.sW - x);
-  const uint8_t* yp = r.src + (long long)y * r.src_pitch + x;
-  const uint8_t* cp = r.src + (long long)(r.sH + (y >> 1)) * r.src_pitch + x;  // pairs of pixels x, x+1, ...
-  uint32_t yw[4], cw[4];
-  if (nv == 16 && ((reinterpret_cast<uintptr_t>(yp) | reinterpret_cast<uintptr_t>(cp)) & 15) == 0) {
-    const uint4 a = __ldg(reinterpret_cast<const uint4*>(yp)), b = __ldg(reinterpret_cast<const uint4*>(cp));
-    yw[0] = a.x; yw[1] = a.y; yw[2] = a.z; yw[3] = a.w;
-    cw[0] = b.x; cw[1] = b.y; cw[2] = b.z; cw[3] = b.w;
+__device__ __forceinline__ void nv12_load16(const uint8_t* p, int nv, bool aligned, uint32_t (&w)[4]) {
+  if (aligned) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) yw[k] = cw[k] = 0u;
+    for (int k = 0; k < 4; ++k) w[k] = 0u;
 #pragma unroll
     for (int k = 0; k < 16; ++k)
-      if (k < nv) {
-        yw[k >> 2] |= uint32_t(__ldg(yp + k)) << (8 * (k & 3));
-        cw[k >> 2] |= uint32_t(__ldg(cp + k)) << (8 * (k & 3));  // nv is even: pairs stay whole
-      }
+      if (k < nv) w[k >> 2] |= uint32_t(__ldg(p + k)) << (8 * (k & 3));
   }
-  uint32_t px[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int Yv = int((yw[k >> 2] >> (8 * (k & 3))) & 0xffu);
-    const int cb = 2 * (k >> 1);  // byte index of this pixel's Cb; Cr follows
-    const int D = int((cw[cb >> 2] >> (8 * (cb & 3))) & 0xffu) - 128;
-    const int E = int((cw[(cb + 1) >> 2] >> (8 * ((cb + 1) & 3))) & 0xffu) - 128;
-    px[k] = nv12_px(Yv, D, E);
-  }
+}
+
+__device__ __forceinline__ void nv12_store48(uint8_t* o, int nv, const uint32_t (&px)[16]) {
   uint32_t ow[12];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {  // 4 pixels (RGB0) -> 3 words
@@ -177,7 +160,6 @@ __global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ Resize
     ow[3 * q + 1] = __byte_perm(px[4 * q + 1], px[4 * q + 2], 0x5421u);
     ow[3 * q + 2] = __byte_perm(px[4 * q + 2], px[4 * q + 3], 0x6542u);
   }
-  uint8_t* o = r.dst + (long long)y * r.dst_pitch + 3LL * x;
   if (nv == 16) {
     uint4* o4 = reinterpret_cast<uint4*>(o);
 #pragma unroll
@@ -187,6 +169,40 @@ __global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ Resize
     for (int i = 0; i < 48; ++i)
       if (i < 3 * nv) o[i] = uint8_t(ow[i >> 2] >> (8 * (i & 3)));
   }
+}
+
+__global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ ResizeJobs jobs) {
+  const ResizeJob& r = jobs.j[blockIdx.y];
+  const unsigned gpr = unsigned(r.sW + 15) / 16u;
+  const unsigned g = blockIdx.x * 256u + threadIdx.x;
+  if (g >= gpr * unsigned(r.sH / 2)) return;
+  const int yp = int(g / gpr), x = int(g - unsigned(yp) * gpr) * 16;
+  const int nv = min(16, r.sW - x);
+  const uint8_t* y0p = r.src + (long long)(2 * yp) * r.src_pitch + x;
+  const uint8_t* y1p = y0p + r.src_pitch;
+  const uint8_t* cp = r.src + (long long)(r.sH + yp) * r.src_pitch + x;  // pairs of pixels x, x+1, ...
+  const bool al = nv == 16 && ((reinterpret_cast<uintptr_t>(y0p) | reinterpret_cast<uintptr_t>(y1p) |
+                                reinterpret_cast<uintptr_t>(cp)) & 15) == 0;
+  uint32_t yw0[4], yw1[4], cw[4];
+  nv12_load16(y0p, nv, al, yw0);
+  nv12_load16(y1p, nv, al, yw1);
+  nv12_load16(cp, nv, al, cw);  // nv is even: pairs stay whole
+  uint32_t px0[16], px1[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    const int D = int((cw[k2 >> 1] >> (16 * (k2 & 1))) & 0xffu) - 128;
+    const int E = int((cw[k2 >> 1] >> (16 * (k2 & 1) + 8)) & 0xffu) - 128;
+    const int cr = 409 * E + 128, cg = -100 * D - 208 * E + 128, cb = 516 * D + 128;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * k2 + h;
+      px0[k] = nv12_px(int((yw0[k >> 2] >> (8 * (k & 3))) & 0xffu), cr, cg, cb);
+      px1[k] = nv12_px(int((yw1[k >> 2] >> (8 * (k & 3))) & 0xffu), cr, cg, cb);
+    }
+  }
+  uint8_t* o = r.dst + (long long)(2 * yp) * r.dst_pitch + 3LL * x;
+  nv12_store48(o, nv, px0);
+  nv12_store48(o + r.dst_pitch, nv, px1);
 }
 
 // Input preparation: resize (any source format) into the plan buffer,
