@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_nv12_rgb(const __grid_constant__ Resize
 // stores when its destination is aligned.
 constexpr int RS_THREADS = 256;
 constexpr int RS_ROWS = 8;                // output rows per block
-constexpr int RS_SMEM_LIMIT = 227 * 1024;  // dynamic shared memory per block
+constexpr int RS_SMEM_LIMIT = 226 * 1024;  // dynamic shared memory per block (227 KB less the static tables)
 // staged bytes of one source row of `bytes` bytes (alignment slack included)
 __host__ __device__ constexpr int rs_row_slot(int bytes) { return (bytes + 15 + 15) & ~15; }
 // one buffer of staged source rows
@@ -253,9 +253,7 @@ __device__ __forceinline__ int rs_stage_row(uint8_t* dst, const uint8_t* src, in
 struct RsRows {
   const uint8_t *row0, *row1, *ch0, *ch1;
 };
-__device__ __forceinline__ RsRows rs_stage(const ResizeJob& r, int y, uint8_t* buf) {
-  int y0, y1, wy;
-  resize_taps(y, r.sH, r.dH, y0, y1, wy);
+__device__ __forceinline__ RsRows rs_stage(const ResizeJob& r, int y0, int y1, uint8_t* buf) {
   RsRows q;
   if (r.nv12) {
     const int ls = rs_row_slot(r.sW);
@@ -289,27 +287,36 @@ __global__ void __launch_bounds__(RS_THREADS) k_resize(const __grid_constant__ R
   uint8_t* src0 = rs_smem_buf + ((4 * r.dW + 15) & ~15);
   const int sb = rs_src_bytes(r.sW, r.nv12);
   uint8_t* orow = src0 + (dbl ? 2 : 1) * sb;
+  // vertical taps of the block's rows, once per block
+  __shared__ int s_yt[RS_ROWS][3];
+  const int ye = min(yb + RS_ROWS, r.dH);
+  if (threadIdx.x < ye - yb) {
+    int y0, y1, wy;
+    resize_taps(yb + int(threadIdx.x), r.sH, r.dH, y0, y1, wy);
+    s_yt[threadIdx.x][0] = y0;
+    s_yt[threadIdx.x][1] = y1;
+    s_yt[threadIdx.x][2] = wy;
+  }
   for (int x = threadIdx.x; x < r.dW; x += RS_THREADS) {
     int x0, x1, wx;
     resize_taps(x, r.sW, r.dW, x0, x1, wx);
     tap[x] = uint32_t(x0) | (uint32_t(x1 - x0) << 14) | (uint32_t(wx) << 15);
   }
-  const int ye = min(yb + RS_ROWS, r.dH);
-  RsRows cur = rs_stage(r, yb, src0);
+  __syncthreads();  // vertical taps visible (the tap table is covered by the first row's barrier)
+  RsRows cur = rs_stage(r, s_yt[0][0], s_yt[0][1], src0);
   cp_async_commit();
   for (int y = yb; y < ye; ++y) {
     RsRows nxt = cur;
     if (dbl) {
       // the next row's copies go to the other buffer, freed after row y - 1
-      if (y + 1 < ye) nxt = rs_stage(r, y + 1, src0 + ((y + 1 - yb) & 1) * sb);
+      if (y + 1 < ye) nxt = rs_stage(r, s_yt[y + 1 - yb][0], s_yt[y + 1 - yb][1], src0 + ((y + 1 - yb) & 1) * sb);
       cp_async_commit();
       cp_async_wait<1>();  // this thread's copies of row y have landed
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();  // every thread's copies of row y (and the tap table) visible; row y - 1 is out
-    int y0, y1, wy;
-    resize_taps(y, r.sH, r.dH, y0, y1, wy);
+    const int wy = s_yt[y - yb][2];
     for (int x = threadIdx.x; x < r.dW; x += RS_THREADS) {
       const uint32_t t = tap[x];
       const int x0 = int(t & 0x3fffu), x1 = x0 + int((t >> 14) & 1u), wx = int(t >> 15);
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resize(const __grid_constant__ R
     }
     __syncthreads();  // output row complete; the buffer of row y is free
     if (!dbl && y + 1 < ye) {
-      nxt = rs_stage(r, y + 1, src0);
+      nxt = rs_stage(r, s_yt[y + 1 - yb][0], s_yt[y + 1 - yb][1], src0);
       cp_async_commit();
     }
     uint8_t* og = r.dst + (long long)y * r.dst_pitch;
