@@ -270,7 +270,7 @@ struct LaunchScope {
 hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s);
 // Copies of unaligned inputs into the plan's aligned buffers (scratch base).
 cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base, cudaStream_t s);
-hz_status set_p1_attributes(hz_ctx* c);
+hz_status set_kernel_attributes(hz_ctx* c);
 HzKParams kparams_of(const hz_params& p);
 hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& jobs);
 hz_status order_after_previous(hz_ctx* c, cudaStream_t s);
