@@ -54,8 +54,10 @@ Readings of points the paper leaves open (each is a parameter here):
       mu the mean BT.601 luminance of the clipped radiance J, so that
       mu^(1/gamma) = 0.5; clamped to [0.5, 2.5] (mu <= 0 gives 2.5, mu >= 1
       gives 0.5). Off by default (fixed gamma, C5).
-* C12 inside the ratio I^c / A^c a channel of A below 1e-6 is floored at
-      1e-6 (only reachable when the selected pixels are black in a channel).
+* C12 a channel of A that is 0 (only reachable when every selected pixel is
+      black in that channel) gives I^c / A^c its limit along A^c -> 0+:
+      +inf where I^c > 0 and 0 where I^c = 0 (0 / A^c = 0 for every
+      A^c > 0); the same for I / max_c A^c of Eq. 4 when A is black.
 
 Parity status: every function here is pinned by tests against closed forms,
 brute force, invariants or hand-worked fixtures, except the colour balance,
@@ -70,7 +72,6 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 GRAY_WEIGHTS = (0.299, 0.587, 0.114)
-A_FLOOR = 1e-6  # reading C12
 
 
 @dataclass
@@ -248,21 +249,39 @@ def ema_airlight(A_hats, lam: float) -> np.ndarray:
 
 # ------------------------------------------------------------- Eq. 4-5 ----
 
+def ratio(In: np.ndarray, a) -> np.ndarray:
+    """In / a for an airlight value a >= 0 (broadcast); a = 0 takes the limit
+    along a -> 0+ (reading C12): +inf where In > 0, 0 where In = 0."""
+    a = np.broadcast_to(np.asarray(a, dtype=np.float64), In.shape)
+    pos = a > 0
+    out = np.where(In > 0, np.inf, 0.0)
+    np.divide(In, a, out=out, where=pos)
+    return out
+
+
 def transmission_dcp(I: np.ndarray, A, omega: float, t0: float, patch: int) -> np.ndarray:
     """t = max(1 - omega * min_{y in Omega(x)} min_c I_n^c(y) / A^c, t0)
-    (the patch form of the transmission, reading C1, with the Eq. 5 clamp)."""
-    A = np.maximum(np.asarray(A, dtype=np.float64), A_FLOOR)
+    (the patch form of the transmission, reading C1, with the Eq. 5 clamp).
+    omega * inf (a black airlight channel) is +inf, so such pixels take t0;
+    omega = 0 gives t = 1."""
+    A = np.asarray(A, dtype=np.float64)
     In = I.astype(np.float64) / 255.0
-    m = (In / A[None, None, :]).min(axis=2)
-    return np.maximum(1.0 - omega * patch_min(m, patch), t0)
+    m = ratio(In, A[None, None, :]).min(axis=2)
+    dm = patch_min(m, patch)
+    if omega == 0.0:
+        return np.ones_like(dm)
+    return np.maximum(1.0 - omega * dm, t0)
 
 
 def transmission_fast(I: np.ndarray, A, omega: float, t0: float) -> np.ndarray:
-    """Eq. 4: that(x) = 1 - omega * min_c I_n^c(x) / max(A); Eq. 5 clamp."""
-    A = np.maximum(np.asarray(A, dtype=np.float64), A_FLOOR)
+    """Eq. 4: that(x) = 1 - omega * min_c I_n^c(x) / max(A); Eq. 5 clamp
+    (a black A takes the limit of reading C12)."""
+    A = np.asarray(A, dtype=np.float64)
     In = I.astype(np.float64) / 255.0
-    that = 1.0 - omega * In.min(axis=2) / A.max()
-    return np.maximum(that, t0)
+    mu = ratio(In.min(axis=2), A.max())
+    if omega == 0.0:
+        return np.ones_like(mu)
+    return np.maximum(1.0 - omega * mu, t0)
 
 
 # ---------------------------------------------------------------- Eq. 6 ----

@@ -361,6 +361,107 @@ def test_image_mode_t_within_bounds():
     assert res.t_coarse is not None
 
 
+# ---- image-mode wiring (Section IV-D, Eq. 6 inside the Section V order) -----
+# Each pin below fixes one link of the composition t -> GuidedFilter(t,
+# gray(I), r, eps) -> clamp [t0, 1] -> Eq. 7 with the refined t, by a case
+# whose answer follows from the guided filter's definition alone.
+
+def _textured_bright(W=37, H=29, seed=41):
+    """Values in [128, 255]: with A = (0.5, 0.5, 0.5) every ratio I/A
+    exceeds 1, so the DCP transmission clamps to t0 everywhere."""
+    g = np.random.default_rng(seed)
+    return g.integers(128, 256, size=(H, W, 3)).astype(np.uint8)
+
+
+def test_image_mode_constant_t_is_kept_and_used():
+    """t = t0 at every pixel (a constant p) => the refined t equals it for any
+    guide (cov(I, p) = 0, mean_p = t0), and J is Eq. 7 with t = t0."""
+    I = _textured_bright()
+    prm = O.OracleParams(gf_radius=5, airlight_override=(0.5, 0.5, 0.5), gamma=1.0)
+    res = O.dehaze_image(I, prm)
+    assert np.all(res.t_coarse == prm.t0)
+    np.testing.assert_allclose(res.t, prm.t0, atol=1e-12)
+    In = I.astype(np.float64) / 255.0
+    J = np.clip((In - 0.5) / prm.t0 + 0.5, 0.0, 1.0)
+    np.testing.assert_allclose(res.J, J, atol=1e-10)
+
+
+def test_image_mode_huge_eps_is_double_box_of_coarse_t():
+    """eps -> inf => a -> 0, b -> mean_p, so the refined t is the box mean of
+    the box mean of the coarse t (clamped), whatever the guide; checked with
+    explicit window loops, and J is reconstructed from the refined t, not the
+    coarse one."""
+    I = hazegen.make_frame(26, 21, seed=17, beta=1.1)
+    prm = O.OracleParams(gf_radius=3, gf_eps=1e12, gamma=1.0)
+    res = O.dehaze_image(I, prm)
+    bb = O.box_mean_brute(O.box_mean_brute(res.t_coarse, 3), 3)
+    np.testing.assert_allclose(res.t, np.clip(bb, prm.t0, 1.0), atol=1e-9)
+    assert np.abs(res.t - res.t_coarse).max() > 1e-3  # the refinement changed t
+    In = I.astype(np.float64) / 255.0
+    J = np.clip((In - res.A) / res.t[..., None] + res.A, 0.0, 1.0)
+    np.testing.assert_allclose(res.J, J, atol=1e-10)
+
+
+def test_image_mode_t_linear_in_grey_guide_is_reproduced():
+    """Grey pixels (r = g = b = v) give gray(I) = v / 255 (the BT.601 weights
+    sum to 1) and, in the Eq. 4 form, t = 1 - omega v / (255 max A): t is an
+    affine function of the guide, so with eps = 0 the guided filter returns
+    it unchanged (He et al. 2013: q = p when p = a I + b)."""
+    g = np.random.default_rng(7)
+    H, W = 24, 30
+    v = (40 + 3 * np.arange(W)[None, :] + 2 * np.arange(H)[:, None] + g.integers(0, 9, size=(H, W))).astype(np.uint8)
+    I = np.repeat(v[..., None], 3, axis=2)
+    A = (0.9, 0.9, 0.9)
+    prm = O.OracleParams(t_mode="fast", omega=0.5, t0=0.05, gf_radius=4, gf_eps=0.0, airlight_override=A)
+    res = O.dehaze_image(I, prm)
+    t_lin = 1.0 - 0.5 * v.astype(np.float64) / 255.0 / 0.9
+    assert t_lin.min() > 0.05  # no clamp inside Eq. 5
+    np.testing.assert_allclose(res.t_coarse, t_lin, atol=1e-12)
+    np.testing.assert_allclose(res.t, t_lin, atol=1e-9)
+
+
+def test_image_mode_guide_is_grey_of_input():
+    """Pixels of one BT.601 luminance but different colours: the guide is
+    constant (var_I = 0, cov = 0 => a = 0) while t varies with the minimum
+    channel, so the refined t is the double box mean of t even for a small
+    eps. Guiding with t itself would instead reproduce t (a ~ 1)."""
+    cols = [(0, 192, 64), (236, 58, 135), (120, 120, 120)]  # 299 r + 587 g + 114 b = 120000
+    assert {299 * c[0] + 587 * c[1] + 114 * c[2] for c in cols} == {120000}
+    H, W = 20, 24
+    g = np.random.default_rng(9)
+    pick = g.integers(0, 3, size=(H, W))
+    I = np.array(cols, np.uint8)[pick]
+    Gd = O.gray(I)
+    assert Gd.max() - Gd.min() < 1e-15  # constant up to rounding
+    prm = O.OracleParams(t_mode="fast", omega=0.8, t0=0.05, gf_radius=3, gf_eps=1e-2,
+                         airlight_override=(0.9, 0.9, 0.9))
+    res = O.dehaze_image(I, prm)
+    assert res.t_coarse.max() - res.t_coarse.min() > 0.1
+    bb = O.box_mean_brute(O.box_mean_brute(res.t_coarse, 3), 3)
+    np.testing.assert_allclose(res.t, bb, atol=1e-12)
+    assert np.abs(res.t - res.t_coarse).max() > 0.05
+
+
+def test_image_mode_clamps_overshoot_to_one():
+    """Repeated bands of red (grey 0.299, t = 1), yellow (grey 0.886, t = 1)
+    and white (grey 1, t = t0): t is concave in the guide, so the local
+    linear fit of every window that spans all three lies above 1 at the red
+    pixels, and the refined t is that q clamped to [t0, 1] (reading C8)."""
+    H, W = 12, 30
+    cols = [(255, 0, 0), (255, 255, 0), (255, 255, 255)]
+    I = np.zeros((H, W, 3), np.uint8)
+    for x in range(W):
+        I[:, x] = cols[(x // 3) % 3]
+    prm = O.OracleParams(t_mode="fast", omega=0.9, t0=0.05, gf_radius=4, gf_eps=1e-4,
+                         airlight_override=(0.9, 0.9, 0.9))
+    res = O.dehaze_image(I, prm)
+    q = O.guided_filter(O.gray(I), res.t_coarse, 4, 1e-4, mean=O.box_mean_brute)
+    over = q > 1.0
+    assert over.any()
+    np.testing.assert_allclose(res.t, np.clip(q, prm.t0, 1.0), atol=1e-12)
+    assert np.all(res.t[over] == 1.0)
+
+
 def test_params_f32_rounding():
     p = O.OracleParams().f32()
     assert p.omega == float(np.float32(0.95))
@@ -368,13 +469,39 @@ def test_params_f32_rounding():
 
 
 def test_transmission_black_airlight_channel_is_finite():
-    """Reading C12: a zero airlight channel is floored inside I/A, so t stays
-    finite and the zero channel (whose ratio is huge) never wins the min."""
+    """Reading C12: a zero airlight channel makes its ratio +inf where the
+    channel is non-zero, so it never wins the minimum."""
     I = np.empty((8, 9, 3), np.uint8)
     I[:] = (40, 30, 20)
     t = O.transmission_dcp(I, [0.5, 0.0, 0.4], 0.95, 0.1, 3)
     assert np.all(np.isfinite(t))
     np.testing.assert_allclose(t, 1 - 0.95 * (20 / 255) / 0.4, rtol=1e-15)
+
+
+def test_transmission_black_airlight_limits():
+    """Reading C12 as the limit A^c -> 0+: I^c / A^c -> +inf for I^c > 0
+    (t -> t0 when that channel is the minimum) and 0 / A^c = 0 for every
+    A^c > 0 (t = 1 wherever that channel is 0); the limits hold for the
+    per-pixel ratio of Eq. 4 with a black airlight too."""
+    I = np.zeros((5, 6, 3), np.uint8)
+    I[:, :3] = (0, 90, 90)    # the black channel of A meets I^r = 0
+    I[:, 3:] = (50, 90, 90)   # I^r > 0: ratio +inf, the others 90/255/0.5
+    A = [0.0, 0.5, 0.5]
+    t = O.transmission_dcp(I, A, 0.95, 0.1, 1)
+    assert np.all(t[:, :3] == 1.0)
+    np.testing.assert_allclose(t[:, 3:], max(1 - 0.95 * (90 / 255) / 0.5, 0.1), rtol=1e-15)
+    # all channels of A black: any non-zero pixel takes t0, a black one t = 1
+    J = np.zeros((4, 4, 3), np.uint8)
+    J[0, 0] = (7, 7, 7)
+    tf = O.transmission_fast(J, [0.0, 0.0, 0.0], 0.5, 0.05)
+    assert tf[0, 0] == 0.05 and np.all(tf.reshape(-1)[1:] == 1.0)
+    td = O.transmission_dcp(J, [0.0, 0.0, 0.0], 0.5, 0.05, 1)
+    assert td[0, 0] == 0.05 and np.all(td.reshape(-1)[1:] == 1.0)
+    # omega = 0 keeps t = 1 even where the ratio is infinite
+    assert np.all(O.transmission_dcp(I, A, 0.0, 0.1, 3) == 1.0)
+    # the limit is approached by small airlight values: a ratio of 1e9 clamps
+    np.testing.assert_allclose(O.transmission_dcp(I, [1e-9, 0.5, 0.5], 0.95, 0.1, 1)[:, 3:],
+                               t[:, 3:], rtol=1e-15)
 
 
 # ---- adaptive gamma (reading C13) -------------------------------------------
