@@ -86,7 +86,7 @@ enum { HZ_MAX_PATCH = 31, HZ_MAX_GF_RADIUS = 255, HZ_MAX_DIM = 16384 };
 typedef struct hz_params {
   uint32_t struct_size;
   int32_t patch;          /* odd, 1..HZ_MAX_PATCH; Section IV-A uses 15 */
-  float omega;            /* haze retention weight, [0, 1]; Eq. 4 */
+  float omega;            /* haze retention weight, 0 or [2^-90, 1]; Eq. 4 */
   float t0;               /* lower bound t_min, [0, 1); Eq. 5 */
   float top_fraction;     /* K = max(1, floor(top_fraction*N)) capped at N;
                              Section IV-B; (0, 1] */
@@ -390,21 +390,31 @@ hz_status hz_get_graph_stats(hz_ctx* ctx, uint64_t* captures, uint64_t* replays)
  *
  * It dehazes one frame in video mode like hz_dehaze_frame with stream_id -1
  * (no smoothing across frames, no hz_ctx needed), and allocates nothing: its
- * scratch is a static 2 MiB device array inside the library, which every GPU
+ * scratch is a static 3 MiB device array inside the library, which every GPU
  * that loads the library holds until the process exits. Frames whose scratch
- * does not fit are rejected with HZ_EINVAL; 854x480 and smaller fit (so does
- * 640x480, the paper's default processing size), 1280x720 does not.
+ * does not fit are rejected with HZ_EINVAL and a message that gives the
+ * bytes needed: 854x480 and smaller fit at any base alignment and pitch (so
+ * does 640x480, the paper's default processing size); 1280x720 fits when
+ * its base and pitch are multiples of 16 bytes (other layouts need an
+ * aligned copy of the frame inside the scratch); 1920x1080 does not.
  *  - p: parameters (as for hz_create); in/out: device pointers, layout as for
  *    every other call; cuda_stream: the stream to enqueue on.
+ *  - info (nullable): when given, the call waits for cuda_stream and fills
+ *    it from the frame's record (A, K, T, S, cut_index, status); a bounded
+ *    device-side wait that gave up returns HZ_EDEVICE_TIMEOUT. The record
+ *    is copied into the caller's struct; nothing is allocated. Without info
+ *    the call returns once the work is enqueued and a device-side timeout
+ *    is not reported.
  *  - The first call on a device looks up the array's device address and sets
  *    kernel attributes; make that first call before any stream capture.
  *  - Every call shares the one array and clears the parts that must start at
  *    zero, so calls whose work overlaps on the GPU (different streams, or
  *    host threads) race and corrupt each other: order them on one stream.
- *  - err (optional, err_len bytes) receives a message on failure. */
+ *  - err (optional, err_len bytes) receives a message on failure, including
+ *    the reason a parameter set was rejected. */
 hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* in, int32_t W, int32_t H,
                                   size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
-                                  char* err, size_t err_len);
+                                  hz_frame_info* info, char* err, size_t err_len);
 
 #ifdef __cplusplus
 }

@@ -147,7 +147,8 @@ _SIGS = {
     "hz_stream_get_state": (C.c_int, [_P, _I, _P, _SZ]),
     "hz_stream_set_state": (C.c_int, [_P, _I, _P, _SZ]),
     "hz_get_server_stats": (C.c_int, [_P, C.POINTER(hz_server_stats)]),
-    "hz_dehaze_frame_noalloc": (C.c_int, [C.POINTER(hz_params), _P, _I, _I, _SZ, _P, _SZ, _P, C.c_char_p, _SZ]),
+    "hz_dehaze_frame_noalloc": (C.c_int, [C.POINTER(hz_params), _P, _I, _I, _SZ, _P, _SZ, _P,
+                                          C.POINTER(hz_frame_info), C.c_char_p, _SZ]),
     "hz_reset_server_stats": (C.c_int, [_P]),
     "hz_set_profiling": (C.c_int, [_P, C.c_int]),
     "hz_set_wave_bytes": (C.c_int, [_P, _SZ]),
@@ -529,15 +530,18 @@ def hz_get_profile(ctx, reset: bool = False) -> dict:
             for k in range(HZ_K_COUNT)}
 
 
-def hz_dehaze_frame_noalloc(p: hz_params, inp, out, stream=None):
-    """The allocation-free single-frame call (static library scratch)."""
+def hz_dehaze_frame_noalloc(p: hz_params, inp, out, stream=None, want_info: bool = False):
+    """The allocation-free single-frame call (static library scratch); with
+    want_info the call waits for the stream and returns the frame's info."""
     pi, W, H, ip = frame_args(inp)
     po, _, _, op = frame_args(out)
     err = C.create_string_buffer(256)
-    st = lib().hz_dehaze_frame_noalloc(C.byref(p), pi, W, H, ip, po, op, _stream_ptr(stream), err, 256)
+    info = hz_frame_info() if want_info else None
+    st = lib().hz_dehaze_frame_noalloc(C.byref(p), pi, W, H, ip, po, op, _stream_ptr(stream),
+                                        C.byref(info) if info is not None else None, err, 256)
     if st != HZ_OK:
         raise HzError(st, f"hz_dehaze_frame_noalloc: {hz_status_str(st)}: {err.value.decode()}")
-    return st
+    return info if want_info else st
 
 
 def hz_reset_server_stats(ctx):

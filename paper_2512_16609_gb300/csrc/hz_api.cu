@@ -395,34 +395,54 @@ extern "C" void hz_params_default(hz_params* p) {
 
 static bool finite_in(float v, float lo, float hi) { return std::isfinite(v) && v >= lo && v <= hi; }
 
-static hz_status validate(hz_ctx* c, const hz_params* p) {
-  if (!p) return fail(c, HZ_EINVAL, "params is NULL");
+// Why a parameter set is invalid: writes the reason into why[0 .. n) and
+// returns true, or returns false for a valid set.
+static bool bad(char* why, size_t n, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(why, n, fmt, ap);
+  va_end(ap);
+  return true;
+}
+
+static bool params_invalid(const hz_params* p, char* why, size_t n) {
+  if (!p) return bad(why, n, "params is NULL");
   if (p->struct_size != sizeof(hz_params))
-    return fail(c, HZ_EINVAL, "struct_size %u != %zu", p->struct_size, sizeof(hz_params));
+    return bad(why, n, "struct_size %u != %zu", p->struct_size, sizeof(hz_params));
   if (p->patch < 1 || p->patch > HZ_MAX_PATCH || (p->patch % 2) == 0)
-    return fail(c, HZ_EINVAL, "patch must be odd in [1, %d]", HZ_MAX_PATCH);
-  if (!finite_in(p->omega, 0.f, 1.f)) return fail(c, HZ_EINVAL, "omega must be in [0, 1]");
-  if (!finite_in(p->t0, 0.f, 0.999f)) return fail(c, HZ_EINVAL, "t0 must be in [0, 1)");
-  if (!(p->top_fraction > 0.f) || !(p->top_fraction <= 1.f)) return fail(c, HZ_EINVAL, "top_fraction must be in (0, 1]");
-  if (!(p->alpha > 0.f) || !(p->alpha <= 4.f)) return fail(c, HZ_EINVAL, "alpha must be in (0, 4]");
-  if (!(p->gamma > 0.f) || !std::isfinite(p->gamma) || p->gamma > 100.f) return fail(c, HZ_EINVAL, "gamma must be in (0, 100]");
-  if (p->t_mode != HZ_T_DCP && p->t_mode != HZ_T_FAST) return fail(c, HZ_EINVAL, "t_mode");
-  if (p->color_balance != 0 && p->color_balance != 1) return fail(c, HZ_EINVAL, "color_balance must be 0 or 1");
-  if (!(p->airlight_ema >= 0.f) || !(p->airlight_ema < 1.f)) return fail(c, HZ_EINVAL, "airlight_ema must be in [0, 1)");
-  if (p->gf_radius < 1 || p->gf_radius > HZ_MAX_GF_RADIUS) return fail(c, HZ_EINVAL, "gf_radius must be in [1, %d]", HZ_MAX_GF_RADIUS);
-  if (!(p->gf_eps >= 0.f) || !std::isfinite(p->gf_eps)) return fail(c, HZ_EINVAL, "gf_eps must be >= 0");
-  if (p->precision != HZ_PREC_FP32 && p->precision != HZ_PREC_FP16) return fail(c, HZ_EINVAL, "precision");
-  if (p->use_airlight_override != 0 && p->use_airlight_override != 1) return fail(c, HZ_EINVAL, "use_airlight_override");
-  if (p->adaptive_gamma != 0 && p->adaptive_gamma != 1) return fail(c, HZ_EINVAL, "adaptive_gamma must be 0 or 1");
+    return bad(why, n, "patch must be odd in [1, %d]", HZ_MAX_PATCH);
+  if (!finite_in(p->omega, 0.f, 1.f) || (p->omega > 0.f && p->omega < OMEGA_MIN_POSITIVE))
+    return bad(why, n, "omega must be 0 or in [2^-90, 1]");
+  if (!finite_in(p->t0, 0.f, 0.999f)) return bad(why, n, "t0 must be in [0, 1)");
+  if (!(p->top_fraction > 0.f) || !(p->top_fraction <= 1.f)) return bad(why, n, "top_fraction must be in (0, 1]");
+  if (!(p->alpha > 0.f) || !(p->alpha <= 4.f)) return bad(why, n, "alpha must be in (0, 4]");
+  if (!(p->gamma > 0.f) || !std::isfinite(p->gamma) || p->gamma > 100.f) return bad(why, n, "gamma must be in (0, 100]");
+  if (p->t_mode != HZ_T_DCP && p->t_mode != HZ_T_FAST) return bad(why, n, "t_mode");
+  if (p->color_balance != 0 && p->color_balance != 1) return bad(why, n, "color_balance must be 0 or 1");
+  if (!(p->airlight_ema >= 0.f) || !(p->airlight_ema < 1.f)) return bad(why, n, "airlight_ema must be in [0, 1)");
+  if (p->gf_radius < 1 || p->gf_radius > HZ_MAX_GF_RADIUS) return bad(why, n, "gf_radius must be in [1, %d]", HZ_MAX_GF_RADIUS);
+  if (!(p->gf_eps >= 0.f) || !std::isfinite(p->gf_eps)) return bad(why, n, "gf_eps must be >= 0");
+  if (p->precision != HZ_PREC_FP32 && p->precision != HZ_PREC_FP16) return bad(why, n, "precision");
+  if (p->use_airlight_override != 0 && p->use_airlight_override != 1) return bad(why, n, "use_airlight_override");
+  if (p->adaptive_gamma != 0 && p->adaptive_gamma != 1) return bad(why, n, "adaptive_gamma must be 0 or 1");
   if (!(p->proc_width == 0 && p->proc_height == 0) &&
       (p->proc_width < 1 || p->proc_height < 1 || p->proc_width > HZ_MAX_DIM || p->proc_height > HZ_MAX_DIM ||
        (long long)p->proc_width * p->proc_height > (1LL << 28)))
-    return fail(c, HZ_EINVAL, "proc_width x proc_height must be 0 x 0 or a valid frame size");
+    return bad(why, n, "proc_width x proc_height must be 0 x 0 or a valid frame size");
   if (p->use_airlight_override)
     for (int k = 0; k < 3; ++k)
       if (!(p->airlight_override[k] > 0.f) || !(p->airlight_override[k] <= 1.f))
-        return fail(c, HZ_EINVAL, "airlight_override must be in (0, 1]");
-  return HZ_OK;
+        return bad(why, n, "airlight_override must be in (0, 1]");
+  return false;
+}
+
+// HZ_EINVAL with the reason in the context's error string (or, with no
+// context, in why[0 .. why_len) when given).
+static hz_status validate(hz_ctx* c, const hz_params* p, char* why = nullptr, size_t why_len = 0) {
+  char buf[256];
+  if (!params_invalid(p, buf, sizeof buf)) return HZ_OK;
+  if (!c && why && why_len) std::snprintf(why, why_len, "%s", buf);
+  return fail(c, HZ_EINVAL, "%s", buf);
 }
 
 extern "C" hz_status hz_params_validate(const hz_params* p) { return validate(nullptr, p); }
@@ -1367,7 +1387,7 @@ extern "C" hz_status hz_get_profile(hz_ctx* c, hz_profile* out, int reset) {
 // address is looked up once per device with cudaGetSymbolAddress.
 
 namespace hz {
-constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(2) << 20;  // 2 MiB per device
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(3) << 20;  // 3 MiB per device
 }  // namespace hz
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[hz::NOALLOC_SCRATCH_BYTES];
@@ -1421,11 +1441,8 @@ hz_status noalloc_setup(int dev, void** out, char* err, size_t len) {
 
 extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* in, int32_t W, int32_t H,
                                              size_t in_pitch, uint8_t* out, size_t out_pitch, void* cuda_stream,
-                                             char* err, size_t err_len) {
-  if (validate(nullptr, p) != HZ_OK) {
-    noalloc_msg(err, err_len, "invalid parameters");
-    return HZ_EINVAL;
-  }
+                                             hz_frame_info* info, char* err, size_t err_len) {
+  if (validate(nullptr, p, err, err_len) != HZ_OK) return HZ_EINVAL;
   if (p->proc_width != 0) {
     noalloc_msg(err, err_len, "no processing-size resize in the allocation-free call");
     return HZ_EINVAL;
@@ -1513,6 +1530,21 @@ extern "C" hz_status hz_dehaze_frame_noalloc(const hz_params* p, const uint8_t* 
   if (e != cudaSuccess) {
     noalloc_msg(err, err_len, "launch failed: %s", cudaGetErrorString(e));
     return HZ_ECUDA;
+  }
+  if (!info) return HZ_OK;
+  // the frame's record, copied to the caller's stack after the stream's work
+  // (a device-to-host copy into pageable memory; nothing is allocated)
+  HzFrameRec rec_h;
+  e = cudaMemcpyAsync(&rec_h, j.rec, sizeof rec_h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    noalloc_msg(err, err_len, "reading the frame record failed: %s", cudaGetErrorString(e));
+    return HZ_ECUDA;
+  }
+  recs_to_infos(&rec_h, lp, 1, info, bal);
+  if (info->status == HZ_EDEVICE_TIMEOUT) {
+    noalloc_msg(err, err_len, "a bounded device-side wait gave up");
+    return HZ_EDEVICE_TIMEOUT;
   }
   return HZ_OK;
 }

@@ -49,7 +49,14 @@ constexpr int GF_HT = 256;      // threads per horizontal-pass block
 // per 32, so that threads GF_HRUN elements apart fall in different banks
 __host__ __device__ constexpr int gf_sidx(int i) { return i + (i >> 5); }
 
-constexpr float A_FLOOR = 1e-6f;  // airlight floor used in ratios I/A
+// Airlight floor inside the ratios I^c / A^c (and I / max_c A^c): a black
+// airlight channel makes the ratio the limit along A^c -> 0+, +inf where
+// I^c > 0 and 0 where I^c = 0. With A^c floored at 2^-100 the ratio of any
+// I^c >= 1 exceeds 2^100 / 255, so for every omega >= 2^-90 (the validator
+// rejects 0 < omega < 2^-90) t takes t0 exactly as in the limit, while
+// I^c = 0 still gives 0; the finite floor avoids 0 * inf = NaN.
+constexpr float A_FLOOR = 7.8886090522101181e-31f;  // 2^-100
+constexpr float OMEGA_MIN_POSITIVE = 8.0779356694631609e-28f;  // 2^-90
 constexpr int HZ_STATUS_SELECT_FAILED = -100;  // per-frame status: selection inconsistent
 constexpr int HZ_STATUS_DEVICE_TIMEOUT = -6;   // per-frame status: a bounded device wait gave up
 

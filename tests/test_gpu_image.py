@@ -21,6 +21,18 @@ pytestmark = pytest.mark.gpu
 #    and q = mean_a I + mean_b: |dq| <~ 2e-3 near t ~ 1.
 TOL_Q32 = 2e-5
 TOL_Q16 = 4e-3
+# uint8 output of the FP16 path. With the refined t off by a relative delta
+# (t' = t (1 + delta)), Eq. 7 gives J' - J = -(J - A) delta / (1 + delta),
+# |J - A| <= 1, and Eq. 8 scales it by (1/gamma) J^(1/gamma - 1) (<= 1 for
+# J >= 0.33 at gamma 1.2, <= 1.8 down to J = 0.01, and J below that maps
+# below 3 LSB where the scale is bounded by the output step itself). The
+# relative error of the FP16 q against the oracle stays below 5e-4 (the
+# stage test reports it: 4.0e-4 at most), so the output moves by at most
+# 255 * 5e-4 * 1.8 = 0.23 LSB before rounding: at most 1 LSB, and exact
+# unless the oracle's value lies within 0.23 LSB of a rounding boundary.
+FP16_MAX_REL_Q = 5e-4
+FP16_MAX_LSB = 1
+FP16_EXACT_MIN = 0.97
 
 
 def report(name, **kv):
@@ -43,8 +55,12 @@ def test_guided_filter_stage(W, H, r, prec):
         qg = q.cpu().numpy().astype(np.float64)
     qr = O.guided_filter(O.gray(I), p.astype(np.float32).astype(np.float64), r, float(np.float32(1e-3)))
     err = np.abs(qg - qr)
-    report("guided_stage", W=W, H=H, r=r, prec=prec, max_abs=float(err.max()), mean_abs=float(err.mean()))
+    rel = err / np.maximum(np.abs(qr), 1e-3)
+    report("guided_stage", W=W, H=H, r=r, prec=prec, max_abs=float(err.max()), mean_abs=float(err.mean()),
+           max_rel=float(rel.max()))
     assert err.max() <= (TOL_Q32 if prec == "fp32" else TOL_Q16)
+    if prec == "fp16":
+        assert rel.max() <= FP16_MAX_REL_Q
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
@@ -63,7 +79,7 @@ def test_image_mode_output(prec, W, H, r, kw):
     if prec == "fp32":
         assert mx <= 1 and exact > 0.99
     else:
-        assert mx <= 4 and exact > 0.9
+        assert mx <= FP16_MAX_LSB and exact > FP16_EXACT_MIN, (mx, exact)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
@@ -77,8 +93,9 @@ def test_image_mode_full_size_4k(prec):
     ref = O.dehaze_image(I, oracle_params(gf_radius=60))
     assert info.T == ref.T and info.cut_index == ref.cut_index
     mx, exact = u8_diff(o, ref.out)
-    report("image_4k", prec=prec, max_lsb=mx, exact_frac=exact)
+    report("image_4k", prec=prec, max_lsb=mx, exact_frac=exact,
+           lsb_hist=[int(v) for v in np.bincount(np.abs(o.astype(int) - ref.out.astype(int)).reshape(-1))])
     if prec == "fp32":
         assert mx <= 1 and exact > 0.99
     else:
-        assert mx <= 4 and exact > 0.9
+        assert mx <= FP16_MAX_LSB and exact > FP16_EXACT_MIN, (mx, exact)

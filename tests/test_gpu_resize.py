@@ -105,5 +105,5 @@ def test_noalloc_rejects_processing_size():
         err = C.create_string_buffer(256)
         pi, W, H, ip = m.binding.frame_args(I)
         po, _, _, op = m.binding.frame_args(out)
-        st = m.binding.lib().hz_dehaze_frame_noalloc(C.byref(prm), pi, W, H, ip, po, op, None, err, 256)
+        st = m.binding.lib().hz_dehaze_frame_noalloc(C.byref(prm), pi, W, H, ip, po, op, None, None, err, 256)
         assert st == m.HZ_EINVAL and b"resize" in err.value

@@ -78,13 +78,50 @@ def test_served_results_equal_alone(host_io):
                                          want_info=True)[0]
                 np.testing.assert_array_equal(outs[k][f], b.cpu().numpy())
                 assert infos[k][f]["A"] == list(info.A)
-    # and the plain streams against the oracle's sequence
-    for k in (0, 1):
-        ref = O.dehaze_sequence(list(seqs[k]), oracle_params(**kw))
+    # and every stream against the oracle's sequence (the guided stream in
+    # image mode, its airlight smoothed across frames like the others)
+    for k, (W, H, fl) in enumerate(STREAMS):
+        ref = _oracle_stream(seqs[k], oracle_params(**kw), bool(fl & 2))
         for f in range(NF):
-            mx, _ = u8_diff(outs[k][f], ref[f].out)
-            assert mx <= 1
+            mx, exact = u8_diff(outs[k][f], ref[f].out)
+            assert mx <= 1 and exact > 0.99
             assert infos[k][f]["T"] == ref[f].T and infos[k][f]["cut_index"] == ref[f].cut_index
+            assert infos[k][f]["S"] == [int(v) for v in ref[f].S]
+
+
+def _oracle_stream(seq, prm, guided):
+    res, A_prev = [], None
+    for I in seq:
+        r = O.dehaze_frame(I, prm, A_prev=A_prev, guided=guided)
+        res.append(r)
+        A_prev = r.A
+    return res
+
+
+def test_served_fp16_guided_stream_matches_oracle():
+    """A served guided stream with FP16 planes (the 4K serving form) against
+    the oracle's image mode: selection bit-exact, output within the FP16
+    bound of the image-mode tests."""
+    from tests.test_gpu_image import FP16_MAX_LSB, FP16_EXACT_MIN
+    kw = dict(airlight_ema=0.9, gf_radius=12, precision="fp16")
+    W, H = 384, 216
+    seq = _frames(W, H, 61)
+    with context(**kw) as (m, ctx):
+        sid = m.hz_open_stream(ctx, W, H, m.HZ_GUIDED)
+        a = torch.from_numpy(seq).pin_memory()
+        b = torch.zeros_like(a).pin_memory()
+        tickets = [m.hz_submit(ctx, sid, a[f], b[f], m.HZ_IO_HOST) for f in range(NF)]
+        infos = []
+        for t in tickets:
+            st, info = m.hz_poll(ctx, t, -1)
+            assert st == m.HZ_OK
+            infos.append(info.as_dict())
+        out = b.numpy().copy()
+    ref = _oracle_stream(seq, oracle_params(**kw), True)
+    for f in range(NF):
+        assert infos[f]["T"] == ref[f].T and infos[f]["cut_index"] == ref[f].cut_index
+        mx, exact = u8_diff(out[f], ref[f].out)
+        assert mx <= FP16_MAX_LSB and exact > FP16_EXACT_MIN, (mx, exact)
 
 
 def test_admission_by_memory_budget():

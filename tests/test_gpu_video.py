@@ -455,3 +455,27 @@ def test_empty_calls():
         z = torch.zeros((0, 32, 32, 3), dtype=torch.uint8, device="cuda")
         assert m.hz_dehaze_video(ctx, z, torch.zeros_like(z)) is None
         assert m.hz_dehaze_batch(ctx, [], []) is None
+
+
+def test_full_size_4k_video_frame_and_mixed_batch():
+    """A 3840x2160 frame in video mode through hz_dehaze_frame, and the same
+    frame inside one hz_dehaze_batch call beside 854x480, 1280x720 and
+    1920x1080 frames (the mixed-batch sizes); every frame against the
+    oracle: selection bit-exact, output within 1 LSB."""
+    specs = [(854, 480, 81), (1280, 720, 82), (1920, 1080, 83), (3840, 2160, 84)]
+    frames = [hazegen.make_frame(W, H, seed=s, beta=0.5 + 0.25 * k) for k, (W, H, s) in enumerate(specs)]
+    refs = [O.dehaze_frame(I, oracle_params()) for I in frames]
+    with context() as (m, ctx):
+        ins = [torch.from_numpy(I).cuda() for I in frames]
+        single = torch.empty_like(ins[3])
+        info4k = m.hz_dehaze_frame(ctx, ins[3], single, want_info=True)
+        outs = [torch.empty_like(x) for x in ins]
+        infos = m.hz_dehaze_batch(ctx, ins, outs, want_info=True)
+        torch.cuda.synchronize()
+        o1 = single.cpu().numpy()
+        ob = [o.cpu().numpy() for o in outs]
+    for info, o, ref in [(info4k, o1, refs[3])] + list(zip(infos, ob, refs)):
+        assert (info.T, info.n_above, info.cut_index) == (ref.T, ref.n_above, ref.cut_index)
+        assert list(info.S) == [int(v) for v in ref.S]
+        mx, exact = u8_diff(o, ref.out)
+        assert mx <= 1 and exact > 0.995, (mx, exact)
