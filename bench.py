@@ -39,8 +39,13 @@ METRIC = "1080p frames/s"
 WORKLOAD = "video 300x1920x1080 RGB u8, patch 15, omega 0.95, t0 0.1, top 0.001, EMA 0.9"
 ALG_BYTES_PER_PX = 6.0  # read I once, write the output once
 # algorithmic bytes per pixel of each kernel class: what its inputs and
-# outputs must move once (dark: I in, P out; recon: I and P in, out written)
-KERNEL_BYTES_PER_PX = {"dark": 6.0, "recon": 9.0, "select": 0.0, "airlight": 0.0}
+# outputs must move once. Fused path: dark = block-minimum bounds (I in, 1/64
+# B/px of block minima out), recon = transmission + reconstruction (I in,
+# output out), select = candidate blocks only. Patch-minimum path: dark = I in,
+# P out; recon = I and P in, output out.
+KERNEL_BYTES_FUSED = {"dark": 3.0 + 1.0 / 64, "recon": 6.0, "select": 0.0, "airlight": 0.0}
+KERNEL_BYTES_PMIN = {"dark": 6.0, "recon": 9.0, "select": 0.0, "airlight": 0.0}
+ISO_FRAMES = 64  # frames of the single-wave call that times each kernel alone
 
 
 def _render_range(args):
@@ -508,35 +513,60 @@ def main():
     ms_step = ms / args.steps
     value = whole_job_value(ms, ws, F, args.steps)
 
-    # ---- per-kernel device time with events on the library's stream ------
+    # ---- per-kernel device time inside the pipelined step (events on each
+    # kernel's own stream; the streams overlap, so a bracket also holds the
+    # time other streams' kernels shared the GPU) ---------------------------
     hzp.hz_set_profiling(ctx, True)
     for _ in range(args.steps):
         hzp.hz_dehaze_video(ctx, inp, out)
     torch.cuda.synchronize()
     hzp.hz_set_profiling(ctx, False)
     kprof = hzp.hz_get_profile(ctx, reset=True)
-    top = max(kprof, key=lambda k: kprof[k]["ms"])
+    # ---- each kernel alone: one wave of ISO_FRAMES frames runs on the call's
+    # stream (no other stream is active), events around every launch -------
+    fused = hzp.hz_get_video_path(ctx)
+    kbytes = KERNEL_BYTES_FUSED if fused else KERNEL_BYTES_PMIN
+    nf_iso = min(F, ISO_FRAMES)
+    wave_saved = hzp.hz_get_wave_bytes(ctx)
+    hzp.hz_set_wave_bytes(ctx, 1 << 30)
+    hzp.hz_set_graph_replay(ctx, False)
+    for _ in range(3):
+        hzp.hz_dehaze_video(ctx, inp[:nf_iso], out[:nf_iso])
+    torch.cuda.synchronize()
+    hzp.hz_set_profiling(ctx, True)
+    for _ in range(args.steps):
+        hzp.hz_dehaze_video(ctx, inp[:nf_iso], out[:nf_iso])
+    torch.cuda.synchronize()
+    hzp.hz_set_profiling(ctx, False)
+    kiso = hzp.hz_get_profile(ctx, reset=True)
+    hzp.hz_set_wave_bytes(ctx, wave_saved)
+    hzp.hz_set_graph_replay(ctx, not args.no_graphs)
     peak, peak_kind = load_peaks()
-    px_step = F * W * H
-    kbytes = KERNEL_BYTES_PER_PX
-    launches_top = max(kprof[top]["timed"], 1)
-    avg_ms = kprof[top]["ms"] / launches_top
-    px_launch = px_step * args.steps / launches_top
-    alg = kbytes.get(top, ALG_BYTES_PER_PX) * px_launch
-    achieved = alg / (avg_ms / 1e3) / 1e9
-    # DRAM bytes per pixel of the top kernel from its ncu capture (a smaller
-    # launch of the same kernel), scaled to this launch's pixels
+    px_iso = nf_iso * W * H
+    iso = {}
+    for k, v in kiso.items():
+        if v["timed"]:
+            avg = v["ms"] / v["timed"]
+            gbs = kbytes.get(k, 0.0) * px_iso / (avg / 1e3) / 1e9
+            iso[k] = {"launches": v["timed"], "avg_ms": avg, "alg_bytes_per_px": kbytes.get(k, 0.0),
+                      "alg_GBps": gbs, "frac": gbs / peak}
+    top = max(iso, key=lambda k: iso[k]["avg_ms"])
+    avg_ms = iso[top]["avg_ms"]
+    px_launch = px_iso
+    achieved = iso[top]["alg_GBps"]
+    # DRAM bytes per pixel of the top kernel from its ncu capture at the
+    # same launch size, times this launch's pixels
     traffic = None
     limiter = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
-                ent = json.load(f).get(top)
+                ent = json.load(f).get("fused" if fused else "pmin", {}).get(top)
             if ent:
                 traffic = ent["bytes_per_px"] * px_launch
                 limiter = ent.get("limiter")
-        except (OSError, ValueError, KeyError, TypeError):
+        except (OSError, ValueError, KeyError, TypeError, AttributeError):
             traffic = None
 
     # ---- e2e: same call with pinned host buffers (copies in the region) ---
@@ -573,7 +603,7 @@ def main():
     if rank == 0:
         emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
              launches, clocks, served, tuning, batch, graphs=not args.no_graphs, variants=variants,
-             limiter=limiter)
+             limiter=limiter, iso=iso, kbytes=kbytes, fused=fused, nf_iso=nf_iso)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -761,7 +791,8 @@ def run_e2e(hzp, ctx, frames_np, out, dev, steps, ws, barrier):
 
 
 def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms, traffic, cpu, e2e,
-         launches, clocks, served=None, tuning=None, batch=None, graphs=False, variants=None, limiter=None):
+         launches, clocks, served=None, tuning=None, batch=None, graphs=False, variants=None, limiter=None,
+         iso=None, kbytes=None, fused=True, nf_iso=ISO_FRAMES):
     if True:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -777,9 +808,17 @@ def emit(args, ws, value, ms_step, kprof, top, achieved, peak, peak_kind, avg_ms
                               "frac_of_measured": value * W * H * ALG_BYTES_PER_PX / 1e9 / peak},
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "alg_bytes_per_px": KERNEL_BYTES_PER_PX.get(top, ALG_BYTES_PER_PX),
-                         "avg_launch_ms": avg_ms,
+                         "alg_bytes_per_px": kbytes.get(top, ALG_BYTES_PER_PX),
+                         "avg_launch_ms": avg_ms, "launch_frames": nf_iso,
+                         "timing": "CUDA events around each launch of a single-wave call on one stream "
+                                   "(the kernel alone)",
+                         "path": {"bytes_per_px": ALG_BYTES_PER_PX,
+                                  "achieved": value * W * H * ALG_BYTES_PER_PX / 1e9,
+                                  "frac": value * W * H * ALG_BYTES_PER_PX / 1e9 / peak,
+                                  "timing": "whole pipelined step, ms_per_step"},
+                         "kernels_alone": iso,
                          "limiter_from_ncu": limiter},
+            "video_path": "fused" if fused else "patch-minimum",
             "kernels": {k: v for k, v in kprof.items() if v["launches"]},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -378,6 +378,18 @@ hz_status hz_set_graph_replay(hz_ctx* ctx, int on);
  * are HZ_EINVAL. */
 #define HZ_INJECT_WITHHOLD_ROW_COPIES 0x1u
 hz_status hz_set_fault_injection(hz_ctx* ctx, uint32_t mask);
+/* Video-mode kernels (Section V's per-frame algorithm either way; the
+ * results are identical, byte for byte). fused = 1 (the default): wherever
+ * the parameters allow it (HZ_T_DCP transmission, fixed gamma, no colour
+ * balance) a frame takes three launches: block minima of min_c I^c with
+ * their histogram (an upper bound of the dark channel of Eq. 2), the exact
+ * dark channel of only the blocks that can reach the top-K level with the
+ * selection and airlight of Eq. 3, and one pass that forms the patch
+ * minimum of min_c I^c/A^c, t (Eq. 4-5), J (Eq. 7), gamma (Eq. 8) and the
+ * output. fused = 0: the per-channel patch-minimum path for every
+ * configuration. Other values: HZ_EINVAL. */
+hz_status hz_set_video_path(hz_ctx* ctx, int fused);
+hz_status hz_get_video_path(const hz_ctx* ctx, int* fused);
 /* Graphs captured and replays done since the context was created. */
 hz_status hz_get_graph_stats(hz_ctx* ctx, uint64_t* captures, uint64_t* replays);
 

@@ -155,6 +155,8 @@ _SIGS = {
     "hz_resize": (C.c_int, [_P, _P, _I, _I, _SZ, _P, _I, _I, _SZ, _P]),
     "hz_autotune_wave_bytes": (C.c_int, [_P, _P, _I, _P, C.POINTER(_SZ), C.POINTER(C.c_float), _I]),
     "hz_set_graph_replay": (C.c_int, [_P, C.c_int]),
+    "hz_set_video_path": (C.c_int, [_P, C.c_int]),
+    "hz_get_video_path": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "hz_set_fault_injection": (C.c_int, [_P, C.c_uint32]),
     "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "hz_get_wave_bytes": (C.c_int, [_P, C.POINTER(_SZ)]),
@@ -492,6 +494,18 @@ def hz_autotune_wave_bytes(ctx, frames, outs, stream_ids=None, guided=None, stre
     _check(lib().hz_autotune_wave_bytes(ctx, descs, len(frames), _stream_ptr(stream), C.byref(best), ms,
                                         len(TUNE_WAVE_MIB)), ctx, "hz_autotune_wave_bytes")
     return int(best.value), {mb: float(ms[i]) for i, mb in enumerate(TUNE_WAVE_MIB)}
+
+
+def hz_set_video_path(ctx, fused: bool):
+    """1: fused video kernels where the parameters allow them; 0: the
+    per-channel patch-minimum path everywhere."""
+    return _check(lib().hz_set_video_path(ctx, 1 if fused else 0), ctx, "hz_set_video_path")
+
+
+def hz_get_video_path(ctx) -> bool:
+    v = C.c_int(0)
+    _check(lib().hz_get_video_path(ctx, C.byref(v)), ctx, "hz_get_video_path")
+    return bool(v.value)
 
 
 def hz_set_graph_replay(ctx, on: bool):

@@ -4,6 +4,7 @@
 
 #include "hz_guided.cuh"
 #include "hz_kernels.cuh"
+#include "hz_video.cuh"
 #include "hz_runtime.cuh"
 
 namespace hz {
@@ -65,6 +66,85 @@ hz_status set_kernel_attributes(hz_ctx* c) {
   static_assert(rs_smem(HZ_MAX_DIM, HZ_MAX_DIM, 0, 1) <= RS_SMEM_LIMIT, "resize staging");
   static_assert(rs_smem(HZ_MAX_DIM, HZ_MAX_DIM, 1, 1) <= RS_SMEM_LIMIT, "resize staging");
   HZ_CK(c, cudaFuncSetAttribute(k_resize, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM_LIMIT));
+  HZ_CK(c, set_v2_attributes());
+  return HZ_OK;
+}
+
+cudaError_t set_v2_attributes() {
+  cudaError_t e = cudaSuccess;
+#define HZ_V2_ATTR(r) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_v2<r>, cudaFuncAttributeMaxDynamicSharedMemorySize, V2S<r>::SMEM);
+  HZ_V2_ATTR(0) HZ_V2_ATTR(1) HZ_V2_ATTR(2) HZ_V2_ATTR(3) HZ_V2_ATTR(4) HZ_V2_ATTR(5) HZ_V2_ATTR(6) HZ_V2_ATTR(7)
+  HZ_V2_ATTR(8) HZ_V2_ATTR(9) HZ_V2_ATTR(10) HZ_V2_ATTR(11) HZ_V2_ATTR(12) HZ_V2_ATTR(13) HZ_V2_ATTR(14) HZ_V2_ATTR(15)
+#undef HZ_V2_ATTR
+  // the selection: its largest window per block size (patch 31 for 8 x 8)
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_smem(0, 0));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_smem(1, 2));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_smem(2, 6));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sel_smem(3, 15));
+  return e;
+}
+
+// The fused video path takes the default video configuration: DCP
+// transmission, fixed gamma, no colour balance.
+bool use_fused(const hz_ctx* c) {
+  return c->fused && c->prm.t_mode == HZ_T_DCP && !c->prm.color_balance && !c->prm.adaptive_gamma;
+}
+
+static int max_v2_tiles(const HzJobs& jobs) {
+  int m = 1;
+  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].v2_tx * jobs.j[i].v2_ty);
+  return m;
+}
+
+// k_b1 + k_sel (the airlight chain in its last block) on s
+hz_status launch_fused_front(hz_ctx* c, HzJobs& jobs, cudaStream_t s, bool bounds, bool select) {
+  const int R = c->prm.patch / 2, LS = bnd_log2(R);
+  const HzKParams kp = kparams_of(c->prm);
+  if (bounds) {
+    int gx = 1, gy = 1;
+    for (int i = 0; i < jobs.n; ++i) {
+      gx = std::max(gx, (int)(((jobs.j[i].W + B1_PX - 1) / B1_PX + B1_THREADS - 1) / B1_THREADS));
+      gy = std::max(gy, jobs.j[i].bnd_h);
+    }
+    LaunchScope ls(c, HZ_K_DARK, s);
+    const dim3 g(gx, gy, jobs.n);
+    switch (LS) {
+      case 0: k_b1<0><<<g, B1_THREADS, 0, s>>>(jobs); break;
+      case 1: k_b1<1><<<g, B1_THREADS, 0, s>>>(jobs); break;
+      case 2: k_b1<2><<<g, B1_THREADS, 0, s>>>(jobs); break;
+      default: k_b1<3><<<g, B1_THREADS, 0, s>>>(jobs); break;
+    }
+    HZ_CK(c, cudaGetLastError());
+  }
+  if (select) {
+    LaunchScope ls(c, HZ_K_SELECT, s);
+    switch (LS) {
+      case 0: k_sel<0><<<dim3(SEL_CL, jobs.n), SEL_THREADS, sel_smem(0, R), s>>>(jobs, kp, R); break;
+      case 1: k_sel<1><<<dim3(SEL_CL, jobs.n), SEL_THREADS, sel_smem(1, R), s>>>(jobs, kp, R); break;
+      case 2: k_sel<2><<<dim3(SEL_CL, jobs.n), SEL_THREADS, sel_smem(2, R), s>>>(jobs, kp, R); break;
+      default: k_sel<3><<<dim3(SEL_CL, jobs.n), SEL_THREADS, sel_smem(3, R), s>>>(jobs, kp, R); break;
+    }
+    HZ_CK(c, cudaGetLastError());
+  }
+  return HZ_OK;
+}
+
+hz_status launch_v2(hz_ctx* c, HzJobs& jobs, cudaStream_t s) {
+  const HzKParams kp = kparams_of(c->prm);
+  const dim3 g(max_v2_tiles(jobs), jobs.n);
+  LaunchScope ls(c, HZ_K_RECON, s);
+  switch (c->prm.patch / 2) {
+#define HZ_V2_CASE(r) \
+  case r: k_v2<r><<<g, V2_NT, V2S<r>::SMEM, s>>>(jobs, kp); break;
+    HZ_V2_CASE(0) HZ_V2_CASE(1) HZ_V2_CASE(2) HZ_V2_CASE(3) HZ_V2_CASE(4) HZ_V2_CASE(5) HZ_V2_CASE(6)
+    HZ_V2_CASE(7) HZ_V2_CASE(8) HZ_V2_CASE(9) HZ_V2_CASE(10) HZ_V2_CASE(11) HZ_V2_CASE(12) HZ_V2_CASE(13)
+    HZ_V2_CASE(14) HZ_V2_CASE(15)
+#undef HZ_V2_CASE
+    default:
+      return fail(c, HZ_EINVAL, "patch radius out of range");
+  }
+  HZ_CK(c, cudaGetLastError());
   return HZ_OK;
 }
 
@@ -131,6 +211,14 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.state = (sid >= 0 && sid < MAX_STREAMS) ? c->states + sid : nullptr;
     j.use_override = c->prm.use_airlight_override;
     j.t_half_out = 0;
+    j.bnd = A + f.off_bnd;
+    j.bnd_pitch = f.bnd_pitch;
+    j.bnd_w = f.bnd_w;
+    j.bnd_h = f.bnd_h;
+    j.v2_tx = v2_tiles_x(c->prm.patch / 2, f.W);
+    j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H);
+    j.dx = A + f.off_P;  // the P region holds the candidates' exact D in the fused path
+    j.dx_pitch = f.P_pitch;
   }
 }
 
@@ -250,6 +338,11 @@ static hz_status run_recon(hz_ctx* c, HzJobs& jobs, bool balance, cudaStream_t s
 }
 
 hz_status run_video_jobs(hz_ctx* c, const LaunchPlan& lp, HzJobs& jobs, bool balance, cudaStream_t s) {
+  if (use_fused(c)) {
+    HZ_CK(c, cudaMemsetAsync(c->arena.base, 0, lp.zero_bytes, s));
+    HZ_TRY(launch_fused_front(c, jobs, s, true, true));
+    return launch_v2(c, jobs, s);
+  }
   hz_status st = run_front(c, lp, jobs, s);
   if (st != HZ_OK) return st;
   return run_recon(c, jobs, balance, s);
@@ -686,6 +779,7 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
     recs = c->rec_pinned;
   }
   const HzKParams kp = kparams_of(c->prm);
+  const bool fused = use_fused(c);
   cudaStream_t sa = c->ps[0], sb = c->ps[1], sc = c->ps[2];
   HZ_CK(c, cudaEventRecord(c->ev_start, s));
   for (int q = 0; q < 3; ++q) HZ_CK(c, cudaStreamWaitEvent(c->ps[q], c->ev_start, 0));
@@ -701,11 +795,14 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
     if (w >= PIPE_SLOTS) HZ_CK(c, cudaStreamWaitEvent(sa, c->ev_free[k], 0));
     HZ_CK(c, cudaMemsetAsync(base, 0, lp.zero_bytes, sa));
     HZ_TRY(prepare_inputs(c, lp, fr + i, m, base, sa));
-    HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(max_tiles(jobs), m), sa, jobs));
+    if (fused) HZ_TRY(launch_fused_front(c, jobs, sa, true, false));
+    else HZ_TRY(launch_p1(c, c->prm.patch / 2, dim3(max_tiles(jobs), m), sa, jobs));
     HZ_CK(c, cudaEventRecord(c->ev_dark[k], sa));
     // stage 2: selection; its last block runs the airlight chain
     HZ_CK(c, cudaStreamWaitEvent(sb, c->ev_dark[k], 0));
-    {
+    if (fused) {
+      HZ_TRY(launch_fused_front(c, jobs, sb, false, true));
+    } else {
       LaunchScope ls(c, HZ_K_SELECT, sb);
       k_p2<<<dim3(P2_BLOCKS, m), 256, 0, sb>>>(jobs, kp);
     }
@@ -713,7 +810,8 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
     HZ_CK(c, cudaEventRecord(c->ev_sel[k], sb));
     // stage 3: reconstruction, then the wave's records
     HZ_CK(c, cudaStreamWaitEvent(sc, c->ev_sel[k], 0));
-    HZ_TRY(run_recon(c, jobs, bal, sc));
+    if (fused) HZ_TRY(launch_v2(c, jobs, sc));
+    else HZ_TRY(run_recon(c, jobs, bal, sc));
     if (recs) HZ_CK(c, cudaMemcpyAsync(recs + i, base, sizeof(HzFrameRec) * size_t(m), cudaMemcpyDeviceToHost, sc));
     HZ_CK(c, cudaEventRecord(c->ev_free[k], sc));
   }
@@ -759,6 +857,7 @@ static std::string call_key(const hz_ctx* c, const void* a, size_t na, const voi
   k.append(reinterpret_cast<const char*>(&c->prm), sizeof c->prm);
   k.append(reinterpret_cast<const char*>(&c->wave_bytes), sizeof c->wave_bytes);
   k.append(reinterpret_cast<const char*>(&c->inject), sizeof c->inject);
+  k.append(reinterpret_cast<const char*>(&c->fused), sizeof c->fused);
   k.append(reinterpret_cast<const char*>(bases), sizeof bases);
   k.append(static_cast<const char*>(a), na);
   if (b) k.append(static_cast<const char*>(b), nb);
@@ -1317,6 +1416,20 @@ extern "C" hz_status hz_set_fault_injection(hz_ctx* c, uint32_t mask) {
   if (mask & ~uint32_t(HZ_INJECT_WITHHOLD_ROW_COPIES)) return fail(c, HZ_EINVAL, "unknown injection mask 0x%x", mask);
   std::lock_guard<std::mutex> lk(c->call_mu);
   c->inject = mask;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_set_video_path(hz_ctx* c, int fused) {
+  if (!c) return HZ_EINVAL;
+  if (fused != 0 && fused != 1) return fail(c, HZ_EINVAL, "video path must be 0 or 1");
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->fused = fused != 0;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_video_path(const hz_ctx* c, int* fused) {
+  if (!c || !fused) return HZ_EINVAL;
+  *fused = c->fused ? 1 : 0;
   return HZ_OK;
 }
 

@@ -38,6 +38,9 @@ inline __host__ __device__ int p3_units(int W, int H) {
   const long long groups = (long long)((W + P3_GPX - 1) / P3_GPX) * H;
   return int((groups + P3_THREADS - 1) / P3_THREADS);
 }
+// ---- fused video path: block size (log2) of the dark-channel bounds for
+// patch radius R, the largest power of two <= R + 1, at most 8 ------------
+__host__ __device__ constexpr int bnd_log2(int R) { return R >= 7 ? 3 : R >= 3 ? 2 : R >= 1 ? 1 : 0; }
 // ---- guided filter ------------------------------------------------------
 constexpr int GF_VBAND = 128;   // output rows per vertical-pass block
 constexpr int GF_VCOLS = 128;   // columns per vertical-pass block
@@ -123,6 +126,12 @@ struct HzJob {
   HzStreamState* state;         // airlight smoothing chain (nullptr: none)
   int use_override;
   int t_half_out;               // M_T_ONLY writes an FP16 plane
+  // fused video path (hz_video.cuh)
+  uint8_t* bnd;                 // block minima of min_c I^c, bnd_h rows of bnd_w
+  int bnd_pitch, bnd_w, bnd_h;
+  int v2_tx, v2_ty;             // k_v2 strips x bands
+  uint8_t* dx;                  // exact dark channel of the selection's candidate blocks
+  long long dx_pitch;
 };
 
 constexpr int MAXJ = 64;  // frames per launch (jobs travel as a kernel parameter)

@@ -15,6 +15,7 @@
 #include "../../include/hazedefy.h"
 #include "hz_internal.cuh"
 
+
 namespace hz {
 
 constexpr int MAX_STREAMS = 256;
@@ -43,6 +44,7 @@ struct hz_ctx {
   hz::Arena stage;            // device staging for host IO
   hz::HzStreamState* states = nullptr;  // [MAX_STREAMS + 1]; last = call-local chain
   hz::HzFrameRec* rec_host = nullptr;   // pinned, MAXJ records
+  bool fused = true;                    // fused video kernels where the parameters allow them
   cudaEvent_t done_ev = nullptr;        // end of the last call's work
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[hz::HOSTIO_BUFS] = {}, ev_comp[hz::HOSTIO_BUFS] = {}, ev_out[hz::HOSTIO_BUFS] = {};
@@ -127,6 +129,8 @@ struct FramePlan {
   long long P_pitch;
   size_t off_rec, off_rowcnt, off_rowsum;  // in the zeroed region
   size_t off_P, off_tilemax, off_bal;      // in the rest
+  size_t off_bnd;                           // block minima of the fused video path
+  int bnd_pitch, bnd_w, bnd_h;
   size_t off_t, off_vs, off_a, off_b, off_q;  // image-mode planes (0 if unused)
   long long plane_pitch32, plane_pitch16;
   size_t off_copy;                          // aligned copy of an unaligned input, or the resized
@@ -201,6 +205,14 @@ inline void plan_frames(const hz_params& prm, const int* Ws, const int* Hs, int 
     o = align_up(o + size_t(f.P_pitch) * f.H, 1024);
     f.off_tilemax = o;
     o = align_up(o + size_t(f.tiles_x) * f.tiles_y, 256);
+    {
+      const int bs = 1 << bnd_log2(prm.patch / 2);
+      f.bnd_w = (f.W + bs - 1) / bs;
+      f.bnd_h = (f.H + bs - 1) / bs;
+      f.bnd_pitch = int(align_up(size_t(f.bnd_w), 16));
+      f.off_bnd = o;
+      o = align_up(o + size_t(f.bnd_pitch) * f.bnd_h, 256);
+    }
     f.off_bal = 0;
     if (balance || prm.adaptive_gamma) {  // per-unit partial sums of the reductions
       f.off_bal = o;
@@ -271,6 +283,8 @@ hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s);
 // Copies of unaligned inputs into the plan's aligned buffers (scratch base).
 cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base, cudaStream_t s);
 hz_status set_kernel_attributes(hz_ctx* c);
+cudaError_t set_v2_attributes();
+bool use_fused(const hz_ctx* c);
 HzKParams kparams_of(const hz_params& p);
 hz_status launch_p1(hz_ctx* c, int R, dim3 grid, cudaStream_t s, const HzJobs& jobs);
 hz_status order_after_previous(hz_ctx* c, cudaStream_t s);

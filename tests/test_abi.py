@@ -97,5 +97,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.hz_poll(None, 1, 0, None) == hzp.HZ_EINVAL
     assert lib.hz_set_fault_injection(None, hzp.HZ_INJECT_WITHHOLD_ROW_COPIES) == hzp.HZ_EINVAL
     assert lib.hz_set_graph_replay(None, 1) == hzp.HZ_EINVAL
+    assert lib.hz_set_video_path(None, 1) == hzp.HZ_EINVAL
+    assert lib.hz_get_video_path(None, None) == hzp.HZ_EINVAL
     assert lib.hz_set_wave_bytes(None, 1 << 20) == hzp.HZ_EINVAL
     assert lib.hz_resize(None, None, 1, 1, 3, None, 1, 1, 3, None) == hzp.HZ_EINVAL
