@@ -130,14 +130,16 @@ __global__ void __launch_bounds__(B1_THREADS) k_b1(const __grid_constant__ HzJob
 constexpr int SEL_CL = 8;         // blocks of a frame's selection cluster
 constexpr int SEL_THREADS = 256;
 constexpr int SEL_WARPS = SEL_THREADS / 32;
-constexpr int SEL_LIST = 4096;   // candidate blocks listed by the first scan
+constexpr int SEL_LIST = 4096;   // candidate blocks listed by a rank's first scan
 constexpr int SEL_CHUNK = 1024;  // blocks listed per pass of a rescan below the list
-constexpr int SEL_RW = 32;       // staged 4-byte words per row of a candidate's region
+// staged 4-byte words per row of a candidate's region (S + 2R pixels of 3
+// bytes, from a word boundary)
+__host__ __device__ constexpr int sel_rw(int LS, int R) { return (3 * ((1 << LS) + 2 * R) + 3 + 3) / 4; }
 constexpr int SEL_VMW = 8 + 2 * 15;  // columns of a candidate's vertical minima
 // dynamic shared memory of k_sel: the list (indices, levels) and one staged
-// region (S + 2R rows of SEL_RW words) per warp
+// region (S + 2R rows of sel_rw words) per warp
 __host__ __device__ constexpr int sel_smem(int LS, int R) {
-  return SEL_LIST * 4 + SEL_LIST + SEL_WARPS * ((1 << LS) + 2 * R) * SEL_RW * 4;
+  return SEL_LIST * 4 + SEL_LIST + SEL_WARPS * ((1 << LS) + 2 * R) * sel_rw(LS, R) * 4;
 }
 
 // Exact D of one candidate block (one warp). The block's region (the block
@@ -157,6 +159,7 @@ __device__ __forceinline__ void sel_block_exact(const HzJob& jb, int R, int b, u
   const int yl = max(Y0 - R, 0), yh = min(Y0 + S + R, H);
   const int wl = (3 * xl) >> 2, nw = ((3 * xh + 3) >> 2) - wl;
   const int nr = yh - yl, ncol = xh - xl;
+  const int rw = sel_rw(LS, R);
   // eight independent loads in flight per lane and batch
   for (int i0 = lane; i0 < nr * nw; i0 += 8 * 32) {
     uint32_t w[8];
@@ -173,7 +176,7 @@ __device__ __forceinline__ void sel_block_exact(const HzJob& jb, int R, int b, u
       const int i = i0 + 32 * u;
       if (i < nr * nw) {
         const int r = i / nw;
-        reg[r * SEL_RW + (i - r * nw)] = w[u];
+        reg[r * rw + (i - r * nw)] = w[u];
       }
     }
   }
@@ -187,7 +190,7 @@ __device__ __forceinline__ void sel_block_exact(const HzJob& jb, int R, int b, u
     const int off = 3 * (xl + c) - 4 * wl;
     auto mrow = [&](int y) -> unsigned {
       if (y < yl || y >= yh) return 0xffu;
-      const uint8_t* q = rb + (y - yl) * SEL_RW * 4 + off;
+      const uint8_t* q = rb + (y - yl) * rw * 4 + off;
       return min(min(unsigned(q[0]), unsigned(q[1])), unsigned(q[2]));
     };
     unsigned core = 0xffu;
@@ -459,7 +462,7 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS)
   __shared__ unsigned s_part[32];
   __shared__ unsigned long long shl[32];
   __shared__ uint8_t vmb[SEL_WARPS][S * SEL_VMW];
-  uint32_t* reg = regs + warp * (S + 2 * R) * SEL_RW;
+  uint32_t* reg = regs + warp * (S + 2 * R) * sel_rw(LS, R);
   unsigned* hxL = cl.map_shared_rank(hx, 0);     // the cluster's exact histogram
   int* spanL = cl.map_shared_rank(s_span, 0);    // the ties' rows and columns
 
