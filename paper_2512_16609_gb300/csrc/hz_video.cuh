@@ -439,7 +439,7 @@ __device__ __forceinline__ void sel_for_blocks(const HzJob& jb, int rank, int lo
 // cluster barrier closes every level round, so all ranks read the same
 // counts and take the same levels. The leader then makes the cut.
 template <int LS>
-__global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS)
+__global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
     k_sel(const __grid_constant__ HzJobs jobs, const HzKParams kp, int R) {
   constexpr int S = 1 << LS;
   namespace cg = cooperative_groups;
