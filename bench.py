@@ -274,7 +274,7 @@ def tune_wave_bytes(hzp, ctx, inp, out, choice):
     outs = [out[f] for f in range(out.shape[0])]
     best, table = hzp.hz_autotune_wave_bytes(ctx, frames, outs)
     return {"wave_mb": best / (1 << 20), "sweep_ms": {str(k): round(v, 4) for k, v in table.items()},
-            "tuner": "hz_autotune_wave_bytes"}
+            "tuner": "hz_autotune_wave_bytes", "video_path": "fused" if hzp.hz_get_video_path(ctx) else "patch-minimum"}
 
 
 def run_variants(hzp, dev, frames_np, reps=10):
@@ -413,6 +413,7 @@ def run_batch_mixed(hzp, dev, frames, reps=10):
                 "ms_per_batch": ms, "frames_per_s": 64 / (ms / 1e3), "mpix_s": npx / (ms / 1e3) / 1e6,
                 "hbm_effective_GBps": npx * ALG_BYTES_PER_PX / (ms / 1e3) / 1e9,
                 "ms_per_batch_without_graph": res["direct"], "wave_mb": best / (1 << 20),
+                "video_path": "fused" if hzp.hz_get_video_path(ctx) else "patch-minimum",
                 "tuner_ms": {str(k): round(v, 4) for k, v in table.items()},
                 "graphs_captured": caps, "graph_replays": replays, "reps": reps}
     finally:
@@ -427,8 +428,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--served-seconds", type=float, default=10.0,
-                    help="length of the served-streams measurement (0 skips it)")
+    ap.add_argument("--served-seconds", type=float, default=5.0,
+                    help="length of each served-streams run (three runs and a loaded one; 0 skips them)")
     ap.add_argument("--wave-mb", default="auto",
                     help="input MiB per wave of frames, or 'auto' for the library autotuner's pick")
     ap.add_argument("--no-graphs", action="store_true", help="time direct calls instead of graph replay")
@@ -628,17 +629,17 @@ def make_served_inputs(nproc):
         return pool.map(_served_frames, specs)
 
 
-def arrivals(seconds, seed=7):
-    """(time, stream index) of Poisson arrivals at SERVED_FPS per stream."""
+def arrivals(seconds, seed=7, scale=1.0):
+    """(time, stream index) of Poisson arrivals at scale x SERVED_FPS per stream."""
     g = np.random.default_rng(seed)
     ev = []
     k = 0
     for (W, H, n, guided) in SERVED_MIX:
         for _ in range(n):
-            t = g.exponential(1.0 / SERVED_FPS)
+            t = g.exponential(1.0 / (scale * SERVED_FPS))
             while t < seconds:
                 ev.append((t, k))
-                t += g.exponential(1.0 / SERVED_FPS)
+                t += g.exponential(1.0 / (scale * SERVED_FPS))
             k += 1
     ev.sort()
     return ev
@@ -657,6 +658,31 @@ def _lat_by_res(by_res):
 
 
 def run_served(hzp, dev, frames_by_res, seconds):
+    """Served streams vs the plain per-frame path: three runs at the
+    workload's arrival rate (median and spread of p50/p99) and one at four
+    times that rate, where batches form."""
+    runs = [run_served_once(hzp, dev, frames_by_res, seconds, seed=7 + k) for k in range(3)]
+    loaded = run_served_once(hzp, dev, frames_by_res, seconds, seed=11, scale=4.0)
+
+    def summary(key):
+        out = {}
+        for q in ("p50_ms", "p99_ms", "frames_per_s"):
+            v = sorted(r[key][q] for r in runs)
+            out[q] = {"median": v[1], "min": v[0], "max": v[2]}
+        return out
+
+    return {"workload": runs[0]["workload"], "runs": 3, "seconds_per_run": seconds,
+            "served": runs[1]["served"] | {"repeats": summary("served")},
+            "plain_fifo": runs[1]["plain_fifo"] | {"repeats": summary("plain_fifo")},
+            "runs_detail": [{"served": {q: r["served"][q] for q in ("p50_ms", "p99_ms", "frames_per_s", "batches",
+                                                                      "frames", "overlapped_batches")},
+                             "plain_fifo": {q: r["plain_fifo"][q] for q in ("p50_ms", "p99_ms", "frames_per_s")}}
+                            for r in runs],
+            "load_4x": {"arrivals": f"4 x {SERVED_FPS:.0f} fps per stream",
+                        "served": loaded["served"], "plain_fifo": loaded["plain_fifo"]}}
+
+
+def run_served_once(hzp, dev, frames_by_res, seconds, seed=7, scale=1.0):
     """Served streams through hz_submit/hz_poll vs the plain per-frame path,
     same arrivals; host (pinned) input and output buffers."""
     import torch
@@ -665,7 +691,7 @@ def run_served(hzp, dev, frames_by_res, seconds):
     for r, (W, H, n, guided) in enumerate(SERVED_MIX):
         kinds += [(r, W, H, guided)] * n
     host_in = [[torch.from_numpy(f).pin_memory() for f in frames_by_res[r]] for r in range(len(SERVED_MIX))]
-    ev = arrivals(seconds)
+    ev = arrivals(seconds, seed, scale)
     # ---- served ----
     ctx = hzp.hz_create(prm, dev.index or 0)
     sids = [hzp.hz_open_stream(ctx, W, H, hzp.HZ_GUIDED if g else 0) for (_, W, H, g) in kinds]
@@ -691,7 +717,8 @@ def run_served(hzp, dev, frames_by_res, seconds):
         by_res[kinds[k][0]].append(info.latency_ms)
     wall = time.perf_counter() - t0
     st = hzp.hz_get_server_stats(ctx)
-    served = {"frames": int(st.frames_done), "batches": int(st.batches), "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+    served = {"frames": int(st.frames_done), "batches": int(st.batches),
+              "overlapped_batches": int(st.overlapped_batches), "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
               "mean_ms": st.mean_ms, "max_ms": st.max_ms, "frames_per_s": st.frames_done / wall,
               "by_resolution": _lat_by_res(by_res)}
     hzp.hz_destroy(ctx)
@@ -728,7 +755,7 @@ def run_served(hzp, dev, frames_by_res, seconds):
     plain = {"frames": len(lat), "p50_ms": pct(0.5), "p99_ms": pct(0.99), "mean_ms": sum(lat) / len(lat),
              "max_ms": lat[-1], "frames_per_s": len(lat) / wall, "by_resolution": _lat_by_res(plain_by_res)}
     return {"workload": "32 streams: 12x1280x720 + 12x1920x1080 video, 8x3840x2160 guided FP16 (r 60), "
-                        f"Poisson {SERVED_FPS:.0f} fps each, {seconds:.0f} s, pinned host I/O",
+                        f"Poisson {scale * SERVED_FPS:.0f} fps each, {seconds:.0f} s, pinned host I/O",
             "served": served, "plain_fifo": plain}
 
 

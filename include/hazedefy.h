@@ -291,6 +291,9 @@ typedef struct hz_server_stats {
   double mean_ms;
   double max_ms;
   double busy_s;       /* wall time from the first submit to the last completion */
+  uint64_t overlapped_batches; /* batches whose input copies or compute began on the
+                                  device before the previous batch's output copies
+                                  had ended (timed CUDA events) */
 } hz_server_stats;
 hz_status hz_get_server_stats(hz_ctx* ctx, hz_server_stats* out);
 /* Clear the latency samples and counters (streams and queues are kept). */
@@ -337,18 +340,20 @@ hz_status hz_get_profile(hz_ctx* ctx, hz_profile* out, int reset);
 hz_status hz_set_wave_bytes(hz_ctx* ctx, size_t bytes);
 hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
 
-/* Wave-size autotuner (no counterpart in the paper): runs the given batch
- * (layout and rules as for hz_dehaze_batch, which it calls) at each
- * candidate wave size, 8, 16, 32, 64, 128, 192, 256, 384 and 512 MiB (a
- * launch takes at most 64 frames whatever the size), two untimed and
- * three timed runs each (CUDA events on cuda_stream), and keeps the fastest
- * as the context's wave size. Every run starts from the stream states at
+/* Autotuner (no counterpart in the paper): runs the given batch (layout and
+ * rules as for hz_dehaze_batch, which it calls) at each candidate wave
+ * size, 8, 16, 32, 64, 128, 192, 256, 384 and 512 MiB (a launch takes at
+ * most 64 frames whatever the size), on each video path that the
+ * parameters allow (fused and patch-minimum, see hz_set_video_path), two
+ * untimed and three timed runs each (CUDA events on cuda_stream), and keeps
+ * the fastest wave size and path as the context's. Every run starts from the stream states at
  * entry, which are restored at the end, so the outputs equal those of one
  * hz_dehaze_batch call and the states are left unchanged. *best_bytes (optional) receives the chosen size; ms_per_candidate
  * (optional, n_candidates >= 9 entries) the mean milliseconds per batch of
  * each candidate. Synchronises the stream. Errors: HZ_EINVAL for a bad frame
  * list or a short ms_per_candidate, HZ_ECUDA / HZ_ENOMEM from the runs (the
- * previous wave size is kept). */
+ * previous wave size and path are kept). ms_per_candidate holds the chosen
+ * path's times. */
 hz_status hz_autotune_wave_bytes(hz_ctx* ctx, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
                                  size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates);
 
@@ -378,6 +383,17 @@ hz_status hz_set_graph_replay(hz_ctx* ctx, int on);
  * are HZ_EINVAL. */
 #define HZ_INJECT_WITHHOLD_ROW_COPIES 0x1u
 hz_status hz_set_fault_injection(hz_ctx* ctx, uint32_t mask);
+/* Tuning records (no counterpart in the paper): a text file of one line per
+ * key, "<key>\tpath=<0|1>\twave_bytes=<n>", the key being the GPU's name,
+ * the batch's distinct frame sizes and the kernel-relevant parameters.
+ * hz_tuning_save writes (or replaces) the line for this batch with the
+ * context's current path and wave size (typically right after
+ * hz_autotune_wave_bytes); hz_tuning_load applies a stored line for this
+ * batch's key and sets *found (nullable) to 1, or leaves the context as it
+ * is and sets 0. Frames are described as for hz_dehaze_batch (only W, H and
+ * flags are read). Errors: HZ_EINVAL (bad arguments, unwritable file). */
+hz_status hz_tuning_save(hz_ctx* ctx, const char* file, const hz_frame_desc* frames, int32_t n);
+hz_status hz_tuning_load(hz_ctx* ctx, const char* file, const hz_frame_desc* frames, int32_t n, int32_t* found);
 /* Video-mode kernels (Section V's per-frame algorithm either way; the
  * results are identical, byte for byte). fused = 1 (the default): wherever
  * the parameters allow it (HZ_T_DCP transmission, fixed gamma, no colour

@@ -94,6 +94,7 @@ class hz_server_stats(C.Structure):
         ("mean_ms", C.c_double),
         ("max_ms", C.c_double),
         ("busy_s", C.c_double),
+        ("overlapped_batches", C.c_uint64),
     ]
 
 
@@ -156,6 +157,8 @@ _SIGS = {
     "hz_autotune_wave_bytes": (C.c_int, [_P, _P, _I, _P, C.POINTER(_SZ), C.POINTER(C.c_float), _I]),
     "hz_set_graph_replay": (C.c_int, [_P, C.c_int]),
     "hz_set_video_path": (C.c_int, [_P, C.c_int]),
+    "hz_tuning_save": (C.c_int, [_P, C.c_char_p, C.POINTER(hz_frame_desc), C.c_int]),
+    "hz_tuning_load": (C.c_int, [_P, C.c_char_p, C.POINTER(hz_frame_desc), C.c_int, C.POINTER(C.c_int)]),
     "hz_get_video_path": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "hz_set_fault_injection": (C.c_int, [_P, C.c_uint32]),
     "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
@@ -494,6 +497,20 @@ def hz_autotune_wave_bytes(ctx, frames, outs, stream_ids=None, guided=None, stre
     _check(lib().hz_autotune_wave_bytes(ctx, descs, len(frames), _stream_ptr(stream), C.byref(best), ms,
                                         len(TUNE_WAVE_MIB)), ctx, "hz_autotune_wave_bytes")
     return int(best.value), {mb: float(ms[i]) for i, mb in enumerate(TUNE_WAVE_MIB)}
+
+
+def hz_tuning_save(ctx, path: str, frames, outs, stream_ids=None, guided=None):
+    """Record the context's video path and wave size for this batch's key."""
+    descs = _descs(frames, outs, stream_ids, guided)
+    return _check(lib().hz_tuning_save(ctx, path.encode(), descs, len(frames)), ctx, "hz_tuning_save")
+
+
+def hz_tuning_load(ctx, path: str, frames, outs, stream_ids=None, guided=None) -> bool:
+    """Apply the recorded path and wave size for this batch's key; True if found."""
+    descs = _descs(frames, outs, stream_ids, guided)
+    found = C.c_int(0)
+    _check(lib().hz_tuning_load(ctx, path.encode(), descs, len(frames), C.byref(found)), ctx, "hz_tuning_load")
+    return bool(found.value)
 
 
 def hz_set_video_path(ctx, fused: bool):

@@ -1,6 +1,9 @@
 // C interface of the Hazedefy library (declared in include/hazedefy.h):
 // context and parameters, the video/batch/image paths and the stage calls.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <string>
 
 #include "hz_guided.cuh"
 #include "hz_kernels.cuh"
@@ -91,10 +94,9 @@ bool use_fused(const hz_ctx* c) {
   return c->fused && c->prm.t_mode == HZ_T_DCP && !c->prm.color_balance && !c->prm.adaptive_gamma;
 }
 
-static int max_v2_tiles(const HzJobs& jobs) {
-  int m = 1;
-  for (int i = 0; i < jobs.n; ++i) m = std::max(m, jobs.j[i].v2_tx * jobs.j[i].v2_ty);
-  return m;
+static int v2_items(const HzJobs& jobs) {
+  const HzJob& last = jobs.j[jobs.n - 1];
+  return last.v2_first + last.v2_tx * last.v2_ty;
 }
 
 // k_b1 + k_sel (the airlight chain in its last block) on s
@@ -102,13 +104,9 @@ hz_status launch_fused_front(hz_ctx* c, HzJobs& jobs, cudaStream_t s, bool bound
   const int R = c->prm.patch / 2, LS = bnd_log2(R);
   const HzKParams kp = kparams_of(c->prm);
   if (bounds) {
-    int gx = 1, gy = 1;
-    for (int i = 0; i < jobs.n; ++i) {
-      gx = std::max(gx, (int)(((jobs.j[i].W + B1_PX - 1) / B1_PX + B1_THREADS - 1) / B1_THREADS));
-      gy = std::max(gy, jobs.j[i].bnd_h);
-    }
+    const HzJob& last = jobs.j[jobs.n - 1];
     LaunchScope ls(c, HZ_K_DARK, s);
-    const dim3 g(gx, gy, jobs.n);
+    const dim3 g(last.b1_first + last.bnd_h * last.b1_xc);
     switch (LS) {
       case 0: k_b1<0><<<g, B1_THREADS, 0, s>>>(jobs); break;
       case 1: k_b1<1><<<g, B1_THREADS, 0, s>>>(jobs); break;
@@ -132,7 +130,7 @@ hz_status launch_fused_front(hz_ctx* c, HzJobs& jobs, cudaStream_t s, bool bound
 
 hz_status launch_v2(hz_ctx* c, HzJobs& jobs, cudaStream_t s) {
   const HzKParams kp = kparams_of(c->prm);
-  const dim3 g(max_v2_tiles(jobs), jobs.n);
+  const dim3 g(v2_items(jobs));
   LaunchScope ls(c, HZ_K_RECON, s);
   switch (c->prm.patch / 2) {
 #define HZ_V2_CASE(r) \
@@ -219,6 +217,15 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H);
     j.dx = A + f.off_P;  // the P region holds the candidates' exact D in the fused path
     j.dx_pitch = f.P_pitch;
+    j.b1_xc = (((j.W + B1_PX - 1) / B1_PX) + B1_THREADS - 1) / B1_THREADS;
+  }
+  // flat grids of the fused kernels: each frame's items follow the previous frame's
+  int v2 = 0, b1 = 0;
+  for (int i = 0; i < n; ++i) {
+    jobs.j[i].v2_first = v2;
+    jobs.j[i].b1_first = b1;
+    v2 += jobs.j[i].v2_tx * jobs.j[i].v2_ty;
+    b1 += jobs.j[i].bnd_h * jobs.j[i].b1_xc;
   }
 }
 
@@ -1368,8 +1375,13 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   HZ_CK(c, cudaMalloc(&saved, sbytes));
   hz_status st = HZ_OK;
   const size_t keep = c->wave_bytes;
+  const bool keep_fused = c->fused;
   size_t best = keep;
+  bool best_fused = keep_fused;
   float best_ms = -1.f;
+  float ms_path[2][NCAND] = {};
+  // both video paths where the parameters let the fused one run
+  const int npath = (c->prm.t_mode == HZ_T_DCP && !c->prm.color_balance && !c->prm.adaptive_gamma) ? 2 : 1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
       cudaMemcpyAsync(saved, c->states, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     st = fail(c, HZ_ECUDA, "autotune setup failed");
@@ -1379,7 +1391,9 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
       return fail(c, HZ_ECUDA, "restoring stream states failed");
     return run_batch(c, frames, n, s, nullptr, nullptr, nullptr);
   };
-  for (int k = 0; k < NCAND && st == HZ_OK; ++k) {
+  for (int pk = 0; pk < npath * NCAND && st == HZ_OK; ++pk) {
+    const int k = pk % NCAND, path = pk / NCAND;
+    c->fused = (npath == 1) ? keep_fused : (path == 0);
     c->wave_bytes = TUNE_WAVE_MIB[k] << 20;
     for (int r = 0; r < 2 && st == HZ_OK; ++r) st = one_run();
     if (st == HZ_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(c, HZ_ECUDA, "event record failed");
@@ -1390,12 +1404,15 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
       st = fail(c, HZ_ECUDA, "event timing failed");
     if (st != HZ_OK) break;
     ms /= 3.f;
-    if (ms_per_candidate) ms_per_candidate[k] = ms;
+    ms_path[path][k] = ms;
     if (best_ms < 0.f || ms < best_ms) {
       best_ms = ms;
       best = c->wave_bytes;
+      best_fused = c->fused;
     }
   }
+  if (ms_per_candidate && st == HZ_OK)
+    for (int k = 0; k < NCAND; ++k) ms_per_candidate[k] = ms_path[(npath == 2 && !best_fused) ? 1 : 0][k];
   if (saved && cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess && st == HZ_OK)
     st = fail(c, HZ_ECUDA, "restoring stream states failed");
   cudaStreamSynchronize(s);
@@ -1403,9 +1420,94 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   c->wave_bytes = (st == HZ_OK) ? best : keep;
+  c->fused = (st == HZ_OK) ? best_fused : keep_fused;
   if (best_bytes) *best_bytes = c->wave_bytes;
   if (st != HZ_OK) return st;
   return mark_done(c, s);
+}
+
+// ---- tuning records: "<key>\tpath=<0|1>\twave_bytes=<n>" lines --------
+// key: the GPU's name, the batch's distinct frame sizes (sorted, '+'
+// joined), and the parameters that change the kernels (transmission form,
+// colour balance, adaptive gamma, patch, guided frames).
+static hz_status tuning_key(hz_ctx* c, const hz_frame_desc* frames, int n, std::string& key) {
+  if (!frames || n <= 0) return fail(c, HZ_EINVAL, "bad frame list");
+  cudaDeviceProp dp;
+  if (cudaGetDeviceProperties(&dp, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HZ_ECUDA, "cudaGetDeviceProperties failed");
+  }
+  std::vector<std::string> sizes;
+  bool guided = false;
+  for (int i = 0; i < n; ++i) {
+    sizes.push_back(std::to_string(frames[i].W) + "x" + std::to_string(frames[i].H) +
+                    ((frames[i].flags & HZ_INPUT_NV12) ? "nv12" : ""));
+    guided = guided || (frames[i].flags & HZ_GUIDED);
+  }
+  std::sort(sizes.begin(), sizes.end());
+  sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+  key = dp.name;
+  key += "|";
+  for (size_t i = 0; i < sizes.size(); ++i) key += (i ? "+" : "") + sizes[i];
+  char mode[96];
+  std::snprintf(mode, sizeof mode, "|%s,bal%d,ag%d,patch%d,guided%d,proc%dx%d",
+                c->prm.t_mode == HZ_T_FAST ? "fast" : "dcp", c->prm.color_balance, c->prm.adaptive_gamma,
+                c->prm.patch, guided ? 1 : 0, c->prm.proc_width, c->prm.proc_height);
+  key += mode;
+  for (char& ch : key)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_tuning_save(hz_ctx* c, const char* file, const hz_frame_desc* frames, int32_t n) {
+  if (!c || !file) return HZ_EINVAL;
+  std::string key;
+  HZ_TRY(tuning_key(c, frames, n, key));
+  std::vector<std::string> lines;
+  if (FILE* f = std::fopen(file, "r")) {
+    char buf[1024];
+    while (std::fgets(buf, sizeof buf, f)) {
+      std::string l(buf);
+      while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+      if (l.empty() || l.compare(0, key.size() + 1, key + "\t") == 0) continue;
+      lines.push_back(l);
+    }
+    std::fclose(f);
+  }
+  lines.push_back(key + "\tpath=" + (c->fused ? "1" : "0") + "\twave_bytes=" + std::to_string(c->wave_bytes));
+  FILE* f = std::fopen(file, "w");
+  if (!f) return fail(c, HZ_EINVAL, "cannot write %s", file);
+  for (const std::string& l : lines) std::fprintf(f, "%s\n", l.c_str());
+  std::fclose(f);
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_tuning_load(hz_ctx* c, const char* file, const hz_frame_desc* frames, int32_t n,
+                                    int32_t* found) {
+  if (!c || !file) return HZ_EINVAL;
+  if (found) *found = 0;
+  std::string key;
+  HZ_TRY(tuning_key(c, frames, n, key));
+  FILE* f = std::fopen(file, "r");
+  if (!f) return HZ_OK;  // no records yet
+  char buf[1024];
+  bool hit = false;
+  int path = 1;
+  unsigned long long wave = 0;
+  while (std::fgets(buf, sizeof buf, f)) {
+    std::string l(buf);
+    if (l.compare(0, key.size() + 1, key + "\t") != 0) continue;
+    if (std::sscanf(l.c_str() + key.size() + 1, "path=%d\twave_bytes=%llu", &path, &wave) == 2 &&
+        (path == 0 || path == 1) && wave >= (1u << 20))
+      hit = true;
+  }
+  std::fclose(f);
+  if (!hit) return HZ_OK;
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->fused = path == 1;
+  c->wave_bytes = size_t(wave);
+  if (found) *found = 1;
+  return HZ_OK;
 }
 
 static_assert(HZ_INJECT_WITHHOLD_ROW_COPIES == unsigned(HZ_INJ_WITHHOLD_ROWS), "injection mask");

@@ -130,6 +130,8 @@ struct HzJob {
   uint8_t* bnd;                 // block minima of min_c I^c, bnd_h rows of bnd_w
   int bnd_pitch, bnd_w, bnd_h;
   int v2_tx, v2_ty;             // k_v2 strips x bands
+  int v2_first, b1_first;       // first work item of the frame in a launch's flat k_v2 / k_b1 grid
+  int b1_xc;                    // k_b1 column chunks per block row
   uint8_t* dx;                  // exact dark channel of the selection's candidate blocks
   long long dx_pitch;
 };
@@ -144,6 +146,19 @@ struct HzJobs {
   int inject;  // HZ_INJ_* mask, 0 in normal operation
   HzJob j[MAXJ];
 };
+
+// The frame of work item i of a flat grid whose frames start at first[]
+// (non-decreasing): the last job with first <= i.
+template <int HzJob::*FIRST>
+__device__ __forceinline__ int job_of_item(const HzJobs& jobs, int i) {
+  int lo = 0, hi = jobs.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs.j[mid].*FIRST <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 // Launch-wide scalar parameters.
 struct HzKParams {

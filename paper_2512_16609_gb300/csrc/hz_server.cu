@@ -41,6 +41,9 @@ struct Slot {
   int order[MAX_BATCH];
   std::vector<Request> reqs;
   cudaEvent_t ev_h2d = nullptr, ev_comp = nullptr, ev_done = nullptr;
+  // timed marks of the batch: its copies in start, its compute starts, its
+  // copies out end (times against the server's reference event)
+  cudaEvent_t t_in = nullptr, t_comp = nullptr, t_out = nullptr;
   hz_status st = HZ_OK;
   bool busy = false;
 };
@@ -57,6 +60,9 @@ struct Server {
   size_t outstanding[MAX_STREAMS] = {0};
   bool stop = false;
   cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_ref = nullptr;     // time origin of the batch marks
+  double prev_out_ms = -1.0;        // when the previous batch's outputs were back
+  uint64_t overlapped = 0;          // batches that began before the previous one ended
   Slot slot[NSLOT];
   std::vector<double> lat_ms;
   uint64_t batches = 0, frames = 0;
@@ -81,6 +87,13 @@ static void complete_loop(Server* S) {
       st = HZ_ECUDA;
     }
     const double t = now_s();
+    // device-side overlap: this batch's copies in (or its compute) began
+    // before the previous batch's copies out had ended
+    float m_in = 0.f, m_comp = 0.f, m_out = 0.f;
+    const bool timed = st == HZ_OK && cudaEventElapsedTime(&m_in, S->ev_ref, sl.t_in) == cudaSuccess &&
+                       cudaEventElapsedTime(&m_comp, S->ev_ref, sl.t_comp) == cudaSuccess &&
+                       cudaEventElapsedTime(&m_out, S->ev_ref, sl.t_out) == cudaSuccess;
+    if (!timed) cudaGetLastError();
     const bool bal = c->prm.color_balance != 0;
     const int n = (int)sl.reqs.size();
     std::vector<hz_frame_info> infos(n);
@@ -106,6 +119,11 @@ static void complete_loop(Server* S) {
       }
       S->frames += n;
       S->t_last = t;
+      if (timed) {
+        const double begin = std::min(double(m_in), double(m_comp));
+        if (S->prev_out_ms >= 0.0 && begin < S->prev_out_ms) S->overlapped += 1;
+        S->prev_out_ms = double(m_out);
+      }
       sl.reqs.clear();
       sl.busy = false;
       S->inflight.pop_front();
@@ -144,6 +162,7 @@ static hz_status launch_batch(Server* S, Slot& sl) {
     sl.stage.base = static_cast<uint8_t*>(p);
     sl.stage.cap = need;
   }
+  HZ_CK(c, cudaEventRecord(sl.t_in, S->s_h2d));
   std::vector<hz_frame_desc> fr(n);
   size_t o = 0;
   bool any_host = false;
@@ -171,6 +190,7 @@ static hz_status launch_batch(Server* S, Slot& sl) {
   }
   HZ_CK(c, cudaEventRecord(sl.ev_h2d, S->s_h2d));
   HZ_CK(c, cudaStreamWaitEvent(S->s_comp, sl.ev_h2d, 0));
+  HZ_CK(c, cudaEventRecord(sl.t_comp, S->s_comp));
   {
     std::lock_guard<std::mutex> lk(c->call_mu);
     cudaSetDevice(c->device);
@@ -190,6 +210,7 @@ static hz_status launch_batch(Server* S, Slot& sl) {
                                  cudaMemcpyDeviceToHost, S->s_d2h));
     }
   }
+  HZ_CK(c, cudaEventRecord(sl.t_out, S->s_d2h));
   HZ_CK(c, cudaEventRecord(sl.ev_done, S->s_d2h));
   return HZ_OK;
 }
@@ -255,8 +276,11 @@ static hz_status server_start(hz_ctx* c) {
     ok = cudaMallocHost(&sl.recs, sizeof(HzFrameRec) * MAX_BATCH) == cudaSuccess &&
          cudaEventCreateWithFlags(&sl.ev_h2d, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&sl.ev_comp, cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming | cudaEventBlockingSync) == cudaSuccess;
+         cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming | cudaEventBlockingSync) == cudaSuccess &&
+         cudaEventCreate(&sl.t_in) == cudaSuccess && cudaEventCreate(&sl.t_comp) == cudaSuccess &&
+         cudaEventCreate(&sl.t_out) == cudaSuccess;
   }
+  ok = ok && cudaEventCreate(&S->ev_ref) == cudaSuccess && cudaEventRecord(S->ev_ref, S->s_h2d) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     c->server = S;
@@ -288,8 +312,12 @@ void server_stop(hz_ctx* c) {
     if (sl.recs) cudaFreeHost(sl.recs);
     if (sl.ev_h2d) cudaEventDestroy(sl.ev_h2d);
     if (sl.ev_comp) cudaEventDestroy(sl.ev_comp);
+    if (sl.t_in) cudaEventDestroy(sl.t_in);
+    if (sl.t_comp) cudaEventDestroy(sl.t_comp);
+    if (sl.t_out) cudaEventDestroy(sl.t_out);
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
   }
+  if (S->ev_ref) cudaEventDestroy(S->ev_ref);
   if (S->s_comp) cudaStreamDestroy(S->s_comp);
   if (S->s_h2d) cudaStreamDestroy(S->s_h2d);
   if (S->s_d2h) cudaStreamDestroy(S->s_d2h);
@@ -470,6 +498,7 @@ extern "C" hz_status hz_get_server_stats(hz_ctx* c, hz_server_stats* out) {
     out->frames_done = S->frames;
     out->batches = S->batches;
     out->busy_s = (S->t_first >= 0) ? S->t_last - S->t_first : 0.0;
+    out->overlapped_batches = S->overlapped;
   }
   if (!lat.empty()) {
     std::sort(lat.begin(), lat.end());
@@ -494,5 +523,7 @@ extern "C" hz_status hz_reset_server_stats(hz_ctx* c) {
   S->batches = 0;
   S->t_first = -1.0;
   S->t_last = 0.0;
+  S->overlapped = 0;
+  S->prev_out_ms = -1.0;
   return HZ_OK;
 }

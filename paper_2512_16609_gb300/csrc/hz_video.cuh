@@ -42,18 +42,22 @@ namespace hz {
 constexpr int B1_THREADS = 128;
 constexpr int B1_PX = 16;  // pixels per thread (48 bytes of a row)
 
+// One work item per (frame, block row, column chunk of B1_THREADS x B1_PX
+// pixels), frames laid end to end in the launch's flat grid.
 template <int LS>
 __global__ void __launch_bounds__(B1_THREADS) k_b1(const __grid_constant__ HzJobs jobs) {
   constexpr int S = 1 << LS;
   constexpr int NB = B1_PX / S;  // blocks per thread
-  const HzJob& jb = jobs.j[blockIdx.z];
+  const int f = job_of_item<&HzJob::b1_first>(jobs, int(blockIdx.x));
+  const HzJob& jb = jobs.j[f];
   const int W = jb.W, H = jb.H;
-  const int by = blockIdx.y;
+  const int item = int(blockIdx.x) - jb.b1_first;
+  const int by = item / jb.b1_xc, cx = item - by * jb.b1_xc;
   __shared__ unsigned sh[256];
   if (by >= jb.bnd_h) return;
   for (int i = threadIdx.x; i < 256; i += B1_THREADS) sh[i] = 0u;
   __syncthreads();
-  const int x = (int(blockIdx.x) * B1_THREADS + int(threadIdx.x)) * B1_PX;
+  const int x = (cx * B1_THREADS + int(threadIdx.x)) * B1_PX;
   if (x < W) {
     const int nv = min(B1_PX, W - x);
     const int y0 = by * S, ny = min(S, H - y0);
@@ -798,11 +802,12 @@ __global__ void __launch_bounds__(V2_NT, V2S<R>::MINB) k_v2(const __grid_constan
   using G = V2S<R>;
   constexpr int P = G::P;
   extern __shared__ __align__(128) unsigned char smem[];
-  const HzJob& jb = jobs.j[blockIdx.y];
+  const HzJob& jb = jobs.j[job_of_item<&HzJob::v2_first>(jobs, int(blockIdx.x))];
   const int W = jb.W, H = jb.H;
   const int tx = jb.v2_tx;
-  if ((int)blockIdx.x >= tx * jb.v2_ty) return;
-  const int strip = blockIdx.x % tx, band = blockIdx.x / tx;
+  const int tile = int(blockIdx.x) - jb.v2_first;  // frames laid end to end in the flat grid
+  if (tile >= tx * jb.v2_ty) return;
+  const int strip = tile % tx, band = tile / tx;
   const int x0 = strip * G::SW, y0 = band * G::BH;
   const int xs = x0 - G::RA;                         // staged column 0
   const int xa = max(xs, 0), xb = min(xs + V2_CT, W);

@@ -117,3 +117,26 @@ def test_autotune_keeps_outputs_and_states():
         torch.cuda.synchronize()
         for a, b in zip(outs, ref):
             assert torch.equal(a, b)
+
+
+def test_tuning_record_roundtrip(tmp_path):
+    """The autotuner's choice (video path and wave size) is recorded per
+    (GPU, frame sizes, mode) and applied again from the file by a new
+    context; a batch with other sizes finds no record."""
+    path = str(tmp_path / "hz_tuning.txt")
+    with context(airlight_ema=0.9) as (m, ctx):
+        ins = _batch_inputs()
+        outs = [empty_dev(W, H, 1)[0] for (W, H, _) in SPECS]
+        best, _ = m.hz_autotune_wave_bytes(ctx, ins, outs)
+        fused = m.hz_get_video_path(ctx)
+        m.hz_tuning_save(ctx, path, ins, outs)
+        m.hz_tuning_save(ctx, path, ins, outs)  # replaces its own line
+    with open(path) as f:
+        assert len(f.read().strip().splitlines()) == 1
+    with context(airlight_ema=0.9) as (m, ctx):
+        m.hz_set_wave_bytes(ctx, 3 << 20)
+        m.hz_set_video_path(ctx, not fused)
+        assert m.hz_tuning_load(ctx, path, ins, outs)
+        assert m.hz_get_wave_bytes(ctx) == best and m.hz_get_video_path(ctx) == fused
+        other = [to_dev(hazegen.make_frame(64, 48, seed=1))]
+        assert not m.hz_tuning_load(ctx, path, other, [empty_dev(64, 48)[0]])
