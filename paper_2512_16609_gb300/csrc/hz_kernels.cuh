@@ -943,63 +943,82 @@ __device__ __forceinline__ void p2_scan_region(const HzJob& jb, int item, int T)
 }
 
 // Airlight of the launch's frames in order: override, or smoothing
-// A_f = lam A_{f-1} + (1 - lam) A_hat_f through each frame's stream state,
-// then the 1/A factors. Loads and stores are spread over the block; the chain
-// runs in one thread on shared memory.
-__device__ void fin_frames(const HzJobs& jobs, const HzKParams& kp) {
-  __shared__ double sAh[MAXJ][3];
-  __shared__ double sA[MAXJ][3];
-  __shared__ HzStreamState* sptr[MAXJ];
-  __shared__ double sst[MAXJ][3];
-  __shared__ long long sfr[MAXJ];
+// A_f = lam A_{f-1} + (1 - lam) A_hat_f through each frame's stream state
+// (C9; the product lam A_{f-1} and the sum each rounded to FP64, in the
+// order the formula is written), then the 1/A factors. The block loads
+// every frame's fields, A_hat and the state it continues into shared memory
+// and forms the products (1 - lam) A_hat_f in parallel; the frames of one
+// state form one chain, run per channel by three threads of the state's
+// first frame in the launch with A in registers (one FP64 multiply and add
+// per frame on its critical path); chains of different states run side by
+// side. sc is shared memory of the calling block.
+struct FinScratch {
+  double sB[MAXJ][3];         // (1 - lam) A_hat_f
+  double sAh[MAXJ][3];
+  double sA[MAXJ][3];
+  HzStreamState* sjs[MAXJ];   // the frame's stream state (null: none or override)
+  double sjA[MAXJ][3];        // that state's A before this launch
+  long long sjf[MAXJ];        // and its frame count
+  int shead[MAXJ];            // first frame of the launch with the same state (-1: none)
+};
+__device__ void fin_frames(const HzJobs& jobs, const HzKParams& kp, FinScratch& sc) {
   const int n = jobs.n, tid = threadIdx.x;
+  const double lam = double(kp.ema);
+  const double one_m_lam = 1.0 - lam;
   for (int f = tid; f < n; f += blockDim.x) {
-    const HzFrameRec* rec = jobs.j[f].rec;
-    sAh[f][0] = __ldcg(&rec->A_hat[0]);
-    sAh[f][1] = __ldcg(&rec->A_hat[1]);
-    sAh[f][2] = __ldcg(&rec->A_hat[2]);
+    const HzJob& jb = jobs.j[f];
+    const HzFrameRec* rec = jb.rec;
+    for (int c = 0; c < 3; ++c) {
+      sc.sAh[f][c] = __ldcg(&rec->A_hat[c]);
+      sc.sB[f][c] = __dmul_rn(one_m_lam, sc.sAh[f][c]);
+    }
+    HzStreamState* st = jb.use_override ? nullptr : jb.state;
+    sc.sjs[f] = st;
+    if (st) {
+      for (int c = 0; c < 3; ++c) sc.sjA[f][c] = __ldcg(&st->A[c]);
+      sc.sjf[f] = __ldcg(&st->frames);
+    }
   }
   __syncthreads();
-  if (tid == 0) {
-    int nst = 0;
-    const double lam = double(kp.ema);
-    for (int f = 0; f < n; ++f) {
-      const HzJob& jb = jobs.j[f];
-      double A[3];
-      if (jb.use_override) {
-        for (int c = 0; c < 3; ++c) A[c] = double(kp.ov[c]);
-      } else if (jb.state) {
-        int k = 0;
-        while (k < nst && sptr[k] != jb.state) ++k;
-        if (k == nst) {
-          sptr[k] = jb.state;
-          for (int c = 0; c < 3; ++c) sst[k][c] = __ldcg(&jb.state->A[c]);
-          sfr[k] = __ldcg(&jb.state->frames);
-          ++nst;
+  for (int f = tid; f < n; f += blockDim.x) {
+    const HzStreamState* st = sc.sjs[f];
+    int h = -1;
+    if (st) {
+      h = f;
+      for (int g = 0; g < f; ++g) {
+        if (sc.sjs[g] == st) {
+          h = g;
+          break;
         }
-        if (kp.ema > 0.f && sfr[k] > 0) {
-          for (int c = 0; c < 3; ++c) A[c] = lam * sst[k][c] + (1.0 - lam) * sAh[f][c];
-        } else {
-          for (int c = 0; c < 3; ++c) A[c] = sAh[f][c];
-        }
-        for (int c = 0; c < 3; ++c) sst[k][c] = A[c];
-        sfr[k] += 1;
-      } else {
-        for (int c = 0; c < 3; ++c) A[c] = sAh[f][c];
       }
-      for (int c = 0; c < 3; ++c) sA[f][c] = A[c];
     }
-    for (int k = 0; k < nst; ++k) {
-      for (int c = 0; c < 3; ++c) sptr[k]->A[c] = sst[k][c];
-      sptr[k]->frames = sfr[k];
+    sc.shead[f] = h;
+    if (!st) {
+      for (int c = 0; c < 3; ++c) sc.sA[f][c] = jobs.j[f].use_override ? double(kp.ov[c]) : sc.sAh[f][c];
     }
+  }
+  __syncthreads();
+  for (int w = tid; w < 3 * n; w += blockDim.x) {
+    const int f = w / 3, c = w - 3 * f;  // a chain's channels on neighbouring lanes
+    if (sc.shead[f] != f) continue;
+    HzStreamState* st = sc.sjs[f];
+    double a = sc.sjA[f][c];
+    long long fr = sc.sjf[f];
+    for (int g = f; g < n; ++g) {
+      if (sc.shead[g] != f) continue;
+      a = (kp.ema > 0.f && fr > 0) ? __dadd_rn(__dmul_rn(lam, a), sc.sB[g][c]) : sc.sAh[g][c];
+      ++fr;
+      sc.sA[g][c] = a;
+    }
+    st->A[c] = a;
+    if (c == 0) st->frames = fr;
   }
   __syncthreads();
   for (int f = tid; f < n; f += blockDim.x) {
     HzFrameRec* rec = jobs.j[f].rec;
     double amax = 0.0;
     for (int c = 0; c < 3; ++c) {
-      const double a = sA[f][c];
+      const double a = sc.sA[f][c];
       rec->A_used[c] = a;
       rec->A[c] = float(a);
       const double af = fmax(double(float(a)), double(A_FLOOR));
@@ -1082,13 +1101,15 @@ __global__ void __launch_bounds__(256) k_p2(const __grid_constant__ HzJobs jobs,
   __syncthreads();
   if (!s_all) return;
   __threadfence();
-  fin_frames(jobs, kp);
+  __shared__ FinScratch fsc;
+  fin_frames(jobs, kp, fsc);
 }
 
 // The airlight chain as its own launch (stage calls that skip selection).
 constexpr int FIN_THREADS = 64;
 __global__ void __launch_bounds__(FIN_THREADS) k_fin(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
-  fin_frames(jobs, kp);
+  __shared__ FinScratch fsc;
+  fin_frames(jobs, kp, fsc);
 }
 
 // ------------------------------------------------------------------------

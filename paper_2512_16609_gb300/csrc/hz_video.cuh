@@ -164,26 +164,16 @@ __device__ __forceinline__ void sel_block_exact(const HzJob& jb, int R, int b, u
   const int wl = (3 * xl) >> 2, nw = ((3 * xh + 3) >> 2) - wl;
   const int nr = yh - yl, ncol = xh - xl;
   const int rw = sel_rw(LS, R);
-  // eight independent loads in flight per lane and batch
-  for (int i0 = lane; i0 < nr * nw; i0 += 8 * 32) {
-    uint32_t w[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + 32 * u;
-      if (i < nr * nw) {
-        const int r = i / nw, q = i - r * nw;
-        w[u] = __ldg(reinterpret_cast<const uint32_t*>(jb.in + (long long)(yl + r) * jb.in_pitch) + wl + q);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + 32 * u;
-      if (i < nr * nw) {
-        const int r = i / nw;
-        reg[r * rw + (i - r * nw)] = w[u];
-      }
-    }
+  // asynchronous 4-byte copies straight into shared memory: every word of
+  // the region in flight at once, one memory latency per block
+  const uint32_t rbase = static_cast<uint32_t>(__cvta_generic_to_shared(reg));
+  for (int i = lane; i < nr * nw; i += 32) {
+    const int r = i / nw, q = i - r * nw;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(jb.in + (long long)(yl + r) * jb.in_pitch) + wl + q;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(rbase + 4u * unsigned(r * rw + q)), "l"(src)
+                 : "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
   const uint8_t* rb = reinterpret_cast<const uint8_t*>(reg);
   // column c: m of every region row; the window of block row r is the block's
@@ -233,14 +223,20 @@ __device__ __forceinline__ void sel_block_exact(const HzJob& jb, int R, int b, u
 }
 
 // Sums of the pixels with D > T and the per-row ties (D == T) of one
-// candidate block (one warp); span[0..3] = the rows and columns the ties
-// occupy (min y, max y, min x, max x).
+// candidate block (one warp). sp[0..3] gathers, per thread, the rows and
+// columns the ties occupy (min y, max y, min x, max x); the block's ties are
+// counted per row in the warp's racc (S rows of count, r, g, b) and go to
+// the frame's row counters with one set of atomics per row.
 template <int LS>
 __device__ __forceinline__ void sel_block_sums(const HzJob& jb, int T, int b, unsigned long long& ar,
-                                               unsigned long long& ag, unsigned long long& ab, int* span) {
+                                               unsigned long long& ag, unsigned long long& ab, int* sp,
+                                               unsigned* racc) {
   constexpr int S = 1 << LS;
   const int lane = threadIdx.x & 31;
   const int X0 = (b % jb.bnd_w) * S, Y0 = (b / jb.bnd_w) * S;
+  if (lane < 4 * S) racc[lane] = 0u;
+  __syncwarp();
+  bool tie = false;
   for (int idx = lane; idx < S * S; idx += 32) {
     const int r = idx / S, j = idx - r * S;
     const int yy = Y0 + r, xx = X0 + j;
@@ -252,16 +248,28 @@ __device__ __forceinline__ void sel_block_sums(const HzJob& jb, int T, int b, un
     if (d > T) {
       ar += r8; ag += g8; ab += b8;
     } else {
-      atomicMin(span + 0, yy);
-      atomicMax(span + 1, yy);
-      atomicMin(span + 2, xx);
-      atomicMax(span + 3, xx);
-      atomicAdd(&jb.rowcnt[yy], 1u);
-      atomicAdd(&jb.rowsum[3 * yy + 0], r8);
-      atomicAdd(&jb.rowsum[3 * yy + 1], g8);
-      atomicAdd(&jb.rowsum[3 * yy + 2], b8);
+      tie = true;
+      sp[0] = min(sp[0], yy);
+      sp[1] = max(sp[1], yy);
+      sp[2] = min(sp[2], xx);
+      sp[3] = max(sp[3], xx);
+      atomicAdd(&racc[4 * r + 0], 1u);
+      atomicAdd(&racc[4 * r + 1], r8);
+      atomicAdd(&racc[4 * r + 2], g8);
+      atomicAdd(&racc[4 * r + 3], b8);
     }
   }
+  if (__any_sync(0xffffffffu, tie)) {
+    __syncwarp();
+    if (lane < S && racc[4 * lane] != 0u) {
+      const int yy = Y0 + lane;
+      atomicAdd(&jb.rowcnt[yy], racc[4 * lane]);
+      atomicAdd(&jb.rowsum[3 * yy + 0], racc[4 * lane + 1]);
+      atomicAdd(&jb.rowsum[3 * yy + 1], racc[4 * lane + 2]);
+      atomicAdd(&jb.rowsum[3 * yy + 2], racc[4 * lane + 3]);
+    }
+  }
+  __syncwarp();
 }
 
 // The frame's cut: the m = K - n_above ties with the lowest raster index.
@@ -466,6 +474,8 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
   __shared__ unsigned s_part[32];
   __shared__ unsigned long long shl[32];
   __shared__ uint8_t vmb[SEL_WARPS][S * SEL_VMW];
+  __shared__ unsigned hd[256];                    // this rank's exact D of the round
+  __shared__ unsigned racc[SEL_WARPS][4 * S];     // a candidate's ties per row
   uint32_t* reg = regs + warp * (S + 2 * R) * sel_rw(LS, R);
   unsigned* hxL = cl.map_shared_rank(hx, 0);     // the cluster's exact histogram
   int* spanL = cl.map_shared_rank(s_span, 0);    // the ties' rows and columns
@@ -474,6 +484,7 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
   // bound of #(D >= u)); sX[u] = sum_{w >= u} hx[w] over the exact D found
   hB[tid] = __ldcg(&rec->hist[tid]);
   hx[tid] = 0u;
+  hd[tid] = 0u;
   if (tid == 0) {
     s_T = -1;
     s_n = 0;
@@ -517,7 +528,12 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
     __syncthreads();
     const int lo = s_lo;
     sel_for_blocks(jb, rank, lo, hi, L0, nlist, list, lvl, cand, &s_nc,
-                   [&](int b) { sel_block_exact<LS>(jb, R, b, hxL, reg, vmb[warp]); });
+                   [&](int b) { sel_block_exact<LS>(jb, R, b, hd, reg, vmb[warp]); });
+    // the round's counts into the cluster histogram, one atomic per level
+    if (hd[tid] != 0u) {
+      atomicAdd(&hxL[tid], hd[tid]);
+      hd[tid] = 0u;
+    }
     cl.sync();
     // exact counts hold for every level >= lo: T is the highest level in
     // [lo, hi) whose count reaches K
@@ -531,8 +547,20 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
   }
   if (T >= 0) {
     unsigned long long ar = 0, ag = 0, ab = 0;
+    int sp[4] = {jb.H, -1, jb.W, -1};
     sel_for_blocks(jb, rank, T, 256, L0, nlist, list, lvl, cand, &s_nc,
-                   [&](int b) { sel_block_sums<LS>(jb, T, b, ar, ag, ab, spanL); });
+                   [&](int b) { sel_block_sums<LS>(jb, T, b, ar, ag, ab, sp, racc[warp]); });
+    // the ties' span: per warp, then one lane of each warp to the leader
+    sp[0] = __reduce_min_sync(0xffffffffu, sp[0]);
+    sp[1] = __reduce_max_sync(0xffffffffu, sp[1]);
+    sp[2] = __reduce_min_sync(0xffffffffu, sp[2]);
+    sp[3] = __reduce_max_sync(0xffffffffu, sp[3]);
+    if ((tid & 31) == 0 && sp[1] >= 0) {
+      atomicMin(spanL + 0, sp[0]);
+      atomicMax(spanL + 1, sp[1]);
+      atomicMin(spanL + 2, sp[2]);
+      atomicMax(spanL + 3, sp[3]);
+    }
     const unsigned long long s0 = block_sum<SEL_WARPS>(ar, shl);
     const unsigned long long s1 = block_sum<SEL_WARPS>(ag, shl);
     const unsigned long long s2 = block_sum<SEL_WARPS>(ab, shl);
@@ -559,7 +587,9 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
   __syncthreads();
   if (!s_all) return;
   __threadfence();
-  fin_frames(jobs, kp);
+  // the list region is free by now: it holds the chain's scratch
+  static_assert(sizeof(FinScratch) <= SEL_LIST * 4, "airlight chain scratch");
+  fin_frames(jobs, kp, *reinterpret_cast<FinScratch*>(sel_dyn));
 }
 
 // ---- transmission and reconstruction ----------------------------------------

@@ -74,6 +74,8 @@ def test_fused_sequence_with_smoothing_and_waves():
     ref = O.dehaze_sequence(list(seq), oracle_params(airlight_ema=0.9))
     for f in range(F):
         assert res[0][2][f] == ref[f].T
+        # A_hat and the smoothing chain round as the oracle's FP64 does
+        assert res[0][1][f] == [float(np.float32(v)) for v in ref[f].A]
         assert u8_diff(res[0][0][f], ref[f].out)[0] <= 1
 
 
