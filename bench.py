@@ -274,7 +274,8 @@ def tune_wave_bytes(hzp, ctx, inp, out, choice):
     outs = [out[f] for f in range(out.shape[0])]
     best, table = hzp.hz_autotune_wave_bytes(ctx, frames, outs)
     return {"wave_mb": best / (1 << 20), "sweep_ms": {str(k): round(v, 4) for k, v in table.items()},
-            "tuner": "hz_autotune_wave_bytes", "video_path": "fused" if hzp.hz_get_video_path(ctx) else "patch-minimum"}
+            "tuner": "hz_autotune_wave_bytes", "video_path": "fused" if hzp.hz_get_video_path(ctx) else "patch-minimum",
+            "band_rows": hzp.hz_get_band_rows(ctx)}
 
 
 def run_variants(hzp, dev, frames_np, reps=10):
@@ -414,6 +415,7 @@ def run_batch_mixed(hzp, dev, frames, reps=10):
                 "hbm_effective_GBps": npx * ALG_BYTES_PER_PX / (ms / 1e3) / 1e9,
                 "ms_per_batch_without_graph": res["direct"], "wave_mb": best / (1 << 20),
                 "video_path": "fused" if hzp.hz_get_video_path(ctx) else "patch-minimum",
+                "band_rows": hzp.hz_get_band_rows(ctx),
                 "tuner_ms": {str(k): round(v, 4) for k, v in table.items()},
                 "graphs_captured": caps, "graph_replays": replays, "reps": reps}
     finally:

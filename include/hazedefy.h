@@ -346,7 +346,10 @@ hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
  * most 64 frames whatever the size), on each video path that the
  * parameters allow (fused and patch-minimum, see hz_set_video_path), two
  * untimed and three timed runs each (CUDA events on cuda_stream), and keeps
- * the fastest wave size and path as the context's. Every run starts from the stream states at
+ * the fastest wave size and path as the context's; when the fused path wins
+ * it then times band heights of 90, 135, 270, 540 and 1080 rows for that
+ * path's stencil kernel (hz_set_band_rows) at the chosen wave size and keeps
+ * the fastest. Every run starts from the stream states at
  * entry, which are restored at the end, so the outputs equal those of one
  * hz_dehaze_batch call and the states are left unchanged. *best_bytes (optional) receives the chosen size; ms_per_candidate
  * (optional, n_candidates >= 9 entries) the mean milliseconds per batch of
@@ -384,10 +387,10 @@ hz_status hz_set_graph_replay(hz_ctx* ctx, int on);
 #define HZ_INJECT_WITHHOLD_ROW_COPIES 0x1u
 hz_status hz_set_fault_injection(hz_ctx* ctx, uint32_t mask);
 /* Tuning records (no counterpart in the paper): a text file of one line per
- * key, "<key>\tpath=<0|1>\twave_bytes=<n>", the key being the GPU's name,
+ * key, "<key>\tpath=<0|1>\twave_bytes=<n>\tband_rows=<n>", the key being the GPU's name,
  * the batch's distinct frame sizes and the kernel-relevant parameters.
  * hz_tuning_save writes (or replaces) the line for this batch with the
- * context's current path and wave size (typically right after
+ * context's current path, wave size and band height (typically right after
  * hz_autotune_wave_bytes); hz_tuning_load applies a stored line for this
  * batch's key and sets *found (nullable) to 1, or leaves the context as it
  * is and sets 0. Frames are described as for hz_dehaze_batch (only W, H and
@@ -406,6 +409,17 @@ hz_status hz_tuning_load(hz_ctx* ctx, const char* file, const hz_frame_desc* fra
  * configuration. Other values: HZ_EINVAL. */
 hz_status hz_set_video_path(hz_ctx* ctx, int fused);
 hz_status hz_get_video_path(const hz_ctx* ctx, int* fused);
+/* Tile shape of the fused path's transmission and reconstruction kernel
+ * (no counterpart in the paper): each block covers a strip of about 240
+ * columns and a band of `rows` output rows, rounded up to whole blocks of
+ * `patch` rows (the vertical minimum is taken in blocks of the window's
+ * height). Taller bands re-read fewer halo rows (2 x (patch / 2) per band)
+ * but give fewer blocks per launch. rows = 0 restores the default (270);
+ * 1..16384 are accepted, others HZ_EINVAL. hz_get_band_rows returns the
+ * height in use (after rounding). Results do not depend on it. The
+ * autotuner sets it (see hz_autotune_wave_bytes). */
+hz_status hz_set_band_rows(hz_ctx* ctx, int32_t rows);
+hz_status hz_get_band_rows(const hz_ctx* ctx, int32_t* rows);
 /* Graphs captured and replays done since the context was created. */
 hz_status hz_get_graph_stats(hz_ctx* ctx, uint64_t* captures, uint64_t* replays);
 

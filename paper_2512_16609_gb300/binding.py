@@ -160,6 +160,8 @@ _SIGS = {
     "hz_tuning_save": (C.c_int, [_P, C.c_char_p, C.POINTER(hz_frame_desc), C.c_int]),
     "hz_tuning_load": (C.c_int, [_P, C.c_char_p, C.POINTER(hz_frame_desc), C.c_int, C.POINTER(C.c_int)]),
     "hz_get_video_path": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "hz_set_band_rows": (C.c_int, [_P, C.c_int32]),
+    "hz_get_band_rows": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "hz_set_fault_injection": (C.c_int, [_P, C.c_uint32]),
     "hz_get_graph_stats": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "hz_get_wave_bytes": (C.c_int, [_P, C.POINTER(_SZ)]),
@@ -523,6 +525,17 @@ def hz_get_video_path(ctx) -> bool:
     v = C.c_int(0)
     _check(lib().hz_get_video_path(ctx, C.byref(v)), ctx, "hz_get_video_path")
     return bool(v.value)
+
+
+def hz_set_band_rows(ctx, rows: int):
+    """Output rows per band of the fused stencil kernel (0: the default)."""
+    return _check(lib().hz_set_band_rows(ctx, int(rows)), ctx, "hz_set_band_rows")
+
+
+def hz_get_band_rows(ctx) -> int:
+    v = C.c_int32(0)
+    _check(lib().hz_get_band_rows(ctx, C.byref(v)), ctx, "hz_get_band_rows")
+    return int(v.value)
 
 
 def hz_set_graph_replay(ctx, on: bool):

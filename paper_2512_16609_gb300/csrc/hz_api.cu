@@ -214,7 +214,8 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.bnd_w = f.bnd_w;
     j.bnd_h = f.bnd_h;
     j.v2_tx = v2_tiles_x(c->prm.patch / 2, f.W);
-    j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H);
+    j.v2_bh = v2_band_rows(c->prm.patch / 2, c->v2_band);
+    j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H, c->v2_band);
     j.dx = A + f.off_P;  // the P region holds the candidates' exact D in the fused path
     j.dx_pitch = f.P_pitch;
     j.b1_xc = (((j.W + B1_PX - 1) / B1_PX) + B1_THREADS - 1) / B1_THREADS;
@@ -865,6 +866,7 @@ static std::string call_key(const hz_ctx* c, const void* a, size_t na, const voi
   k.append(reinterpret_cast<const char*>(&c->wave_bytes), sizeof c->wave_bytes);
   k.append(reinterpret_cast<const char*>(&c->inject), sizeof c->inject);
   k.append(reinterpret_cast<const char*>(&c->fused), sizeof c->fused);
+  k.append(reinterpret_cast<const char*>(&c->v2_band), sizeof c->v2_band);
   k.append(reinterpret_cast<const char*>(bases), sizeof bases);
   k.append(static_cast<const char*>(a), na);
   if (b) k.append(static_cast<const char*>(b), nb);
@@ -1352,6 +1354,8 @@ extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
 // are restored at the end: the tuning leaves no trace beyond the outputs,
 // which equal those of one ordinary call.
 static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256, 384, 512};
+// band heights of the fused stencil kernel (rows; a multiple of the patch side is taken)
+static const int TUNE_BAND_ROWS[] = {90, 135, 270, 540, 1080};
 
 extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
                                             size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates) {
@@ -1376,6 +1380,7 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   hz_status st = HZ_OK;
   const size_t keep = c->wave_bytes;
   const bool keep_fused = c->fused;
+  const int keep_band = c->v2_band;
   size_t best = keep;
   bool best_fused = keep_fused;
   float best_ms = -1.f;
@@ -1411,6 +1416,30 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
       best_fused = c->fused;
     }
   }
+  // the stencil kernel's band height, on the fused path at the chosen wave size
+  int best_band = keep_band;
+  if (st == HZ_OK && best_fused && npath == 2) {
+    c->fused = true;
+    c->wave_bytes = best;
+    for (int k = 0; k < int(sizeof TUNE_BAND_ROWS / sizeof TUNE_BAND_ROWS[0]) && st == HZ_OK; ++k) {
+      c->v2_band = TUNE_BAND_ROWS[k];
+      if (c->v2_band == keep_band) continue;  // timed in the sweep above
+      for (int r = 0; r < 2 && st == HZ_OK; ++r) st = one_run();
+      if (st == HZ_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(c, HZ_ECUDA, "event record failed");
+      for (int r = 0; r < 3 && st == HZ_OK; ++r) st = one_run();
+      float ms = 0.f;
+      if (st == HZ_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = fail(c, HZ_ECUDA, "event timing failed");
+      if (st != HZ_OK) break;
+      ms /= 3.f;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_band = c->v2_band;
+      }
+    }
+  }
+  c->v2_band = (st == HZ_OK) ? best_band : keep_band;
   if (ms_per_candidate && st == HZ_OK)
     for (int k = 0; k < NCAND; ++k) ms_per_candidate[k] = ms_path[(npath == 2 && !best_fused) ? 1 : 0][k];
   if (saved && cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess && st == HZ_OK)
@@ -1474,7 +1503,8 @@ extern "C" hz_status hz_tuning_save(hz_ctx* c, const char* file, const hz_frame_
     }
     std::fclose(f);
   }
-  lines.push_back(key + "\tpath=" + (c->fused ? "1" : "0") + "\twave_bytes=" + std::to_string(c->wave_bytes));
+  lines.push_back(key + "\tpath=" + (c->fused ? "1" : "0") + "\twave_bytes=" + std::to_string(c->wave_bytes) +
+                  "\tband_rows=" + std::to_string(c->v2_band));
   FILE* f = std::fopen(file, "w");
   if (!f) return fail(c, HZ_EINVAL, "cannot write %s", file);
   for (const std::string& l : lines) std::fprintf(f, "%s\n", l.c_str());
@@ -1492,20 +1522,27 @@ extern "C" hz_status hz_tuning_load(hz_ctx* c, const char* file, const hz_frame_
   if (!f) return HZ_OK;  // no records yet
   char buf[1024];
   bool hit = false;
-  int path = 1;
+  int path = 1, band = V2_BAND;
   unsigned long long wave = 0;
   while (std::fgets(buf, sizeof buf, f)) {
     std::string l(buf);
     if (l.compare(0, key.size() + 1, key + "\t") != 0) continue;
-    if (std::sscanf(l.c_str() + key.size() + 1, "path=%d\twave_bytes=%llu", &path, &wave) == 2 &&
-        (path == 0 || path == 1) && wave >= (1u << 20))
+    int p = 1, b = V2_BAND;
+    unsigned long long w = 0;
+    const int got = std::sscanf(l.c_str() + key.size() + 1, "path=%d\twave_bytes=%llu\tband_rows=%d", &p, &w, &b);
+    if (got >= 2 && (p == 0 || p == 1) && w >= (1u << 20) && b >= 1 && b <= V2_BAND_MAX) {
+      path = p;
+      wave = w;
+      band = (got == 3) ? b : V2_BAND;
       hit = true;
+    }
   }
   std::fclose(f);
   if (!hit) return HZ_OK;
   std::lock_guard<std::mutex> lk(c->call_mu);
   c->fused = path == 1;
   c->wave_bytes = size_t(wave);
+  c->v2_band = band;
   if (found) *found = 1;
   return HZ_OK;
 }
@@ -1532,6 +1569,20 @@ extern "C" hz_status hz_set_video_path(hz_ctx* c, int fused) {
 extern "C" hz_status hz_get_video_path(const hz_ctx* c, int* fused) {
   if (!c || !fused) return HZ_EINVAL;
   *fused = c->fused ? 1 : 0;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_set_band_rows(hz_ctx* c, int32_t rows) {
+  if (!c) return HZ_EINVAL;
+  if (rows < 0 || rows > V2_BAND_MAX) return fail(c, HZ_EINVAL, "band rows must be in 0..%d", V2_BAND_MAX);
+  std::lock_guard<std::mutex> lk(c->call_mu);
+  c->v2_band = rows ? rows : V2_BAND;
+  return HZ_OK;
+}
+
+extern "C" hz_status hz_get_band_rows(const hz_ctx* c, int32_t* rows) {
+  if (!c || !rows) return HZ_EINVAL;
+  *rows = v2_band_rows(c->prm.patch / 2, c->v2_band);
   return HZ_OK;
 }
 

@@ -130,6 +130,7 @@ struct HzJob {
   uint8_t* bnd;                 // block minima of min_c I^c, bnd_h rows of bnd_w
   int bnd_pitch, bnd_w, bnd_h;
   int v2_tx, v2_ty;             // k_v2 strips x bands
+  int v2_bh;                    // k_v2 output rows per band (a multiple of the patch side)
   int v2_first, b1_first;       // first work item of the frame in a launch's flat k_v2 / k_b1 grid
   int b1_xc;                    // k_b1 column chunks per block row
   uint8_t* dx;                  // exact dark channel of the selection's candidate blocks

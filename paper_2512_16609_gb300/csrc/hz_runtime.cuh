@@ -45,6 +45,7 @@ struct hz_ctx {
   hz::HzStreamState* states = nullptr;  // [MAX_STREAMS + 1]; last = call-local chain
   hz::HzFrameRec* rec_host = nullptr;   // pinned, MAXJ records
   bool fused = true;                    // fused video kernels where the parameters allow them
+  int v2_band = 270;                    // requested output rows per band of the fused stencil kernel
   cudaEvent_t done_ev = nullptr;        // end of the last call's work
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[hz::HOSTIO_BUFS] = {}, ev_comp[hz::HOSTIO_BUFS] = {}, ev_out[hz::HOSTIO_BUFS] = {};

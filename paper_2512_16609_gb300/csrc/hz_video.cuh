@@ -597,15 +597,14 @@ constexpr int V2_CT = 256;          // compute threads: one staged column each
 constexpr int V2_NT = V2_CT + 32;   // and one producer warp
 constexpr int V2_SLOT = 816;        // bytes per staged row (16 x odd)
 constexpr int V2_VST = 260;         // floats per row of vertical minima
-constexpr int V2_BAND = 270;        // output rows per band (about)
+constexpr int V2_BAND = 270;        // default output rows per band (about; a multiple of P is taken)
+constexpr int V2_BAND_MAX = 16384;  // largest band height a context accepts
 
 template <int R>
 struct V2S {
   static constexpr int P = 2 * R + 1;
   static constexpr int SW = ((V2_CT - 2 * R) / 16) * 16;  // output columns per strip
   static constexpr int RA = (V2_CT - SW) / 2;             // staged columns left of the strip
-  static constexpr int M = (V2_BAND + P - 1) / P;         // vHGW blocks per band
-  static constexpr int BH = M * P;                        // output rows per band
   static constexpr int NSEG = SW / 16;
   static constexpr int S0 = 16 + ((-3 * RA) & 15);        // slot byte of staged byte 0
   static constexpr int OFFQ = (RA - R) & ~3;              // first V word of a segment's loads
@@ -634,8 +633,14 @@ __host__ __device__ inline int v2_tiles_x(int R, int W) {
   const int sw = ((V2_CT - 2 * R) / 16) * 16;
   return (W + sw - 1) / sw;
 }
-__host__ __device__ inline int v2_tiles_y(int R, int H) {
-  const int P = 2 * R + 1, bh = ((V2_BAND + P - 1) / P) * P;
+// output rows per band: the requested height rounded up to whole vHGW
+// blocks of P rows
+__host__ __device__ inline int v2_band_rows(int R, int rows) {
+  const int P = 2 * R + 1;
+  return ((rows + P - 1) / P) * P;
+}
+__host__ __device__ inline int v2_tiles_y(int R, int H, int rows) {
+  const int bh = v2_band_rows(R, rows);
   return (H + bh - 1) / bh;
 }
 
@@ -838,11 +843,11 @@ __global__ void __launch_bounds__(V2_NT, V2S<R>::MINB) k_v2(const __grid_constan
   const int tile = int(blockIdx.x) - jb.v2_first;  // frames laid end to end in the flat grid
   if (tile >= tx * jb.v2_ty) return;
   const int strip = tile % tx, band = tile / tx;
-  const int x0 = strip * G::SW, y0 = band * G::BH;
+  const int x0 = strip * G::SW, y0 = band * jb.v2_bh;
   const int xs = x0 - G::RA;                         // staged column 0
   const int xa = max(xs, 0), xb = min(xs + V2_CT, W);
   const int ya = y0 - R;                             // staged row 0
-  const int rows_out = min(G::BH, H - y0);
+  const int rows_out = min(jb.v2_bh, H - y0);
   const int kmax = (rows_out - 1) / P + 1;           // last block iteration
   float* V = reinterpret_cast<float*>(smem + G::OFF_V);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + G::OFF_MBAR);

@@ -99,5 +99,7 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.hz_set_graph_replay(None, 1) == hzp.HZ_EINVAL
     assert lib.hz_set_video_path(None, 1) == hzp.HZ_EINVAL
     assert lib.hz_get_video_path(None, None) == hzp.HZ_EINVAL
+    assert lib.hz_set_band_rows(None, 270) == hzp.HZ_EINVAL
+    assert lib.hz_get_band_rows(None, None) == hzp.HZ_EINVAL
     assert lib.hz_set_wave_bytes(None, 1 << 20) == hzp.HZ_EINVAL
     assert lib.hz_resize(None, None, 1, 1, 3, None, 1, 1, 3, None) == hzp.HZ_EINVAL

@@ -120,7 +120,7 @@ def test_autotune_keeps_outputs_and_states():
 
 
 def test_tuning_record_roundtrip(tmp_path):
-    """The autotuner's choice (video path and wave size) is recorded per
+    """The autotuner's choice (video path, wave size, band height) is recorded per
     (GPU, frame sizes, mode) and applied again from the file by a new
     context; a batch with other sizes finds no record."""
     path = str(tmp_path / "hz_tuning.txt")
@@ -129,6 +129,7 @@ def test_tuning_record_roundtrip(tmp_path):
         outs = [empty_dev(W, H, 1)[0] for (W, H, _) in SPECS]
         best, _ = m.hz_autotune_wave_bytes(ctx, ins, outs)
         fused = m.hz_get_video_path(ctx)
+        band = m.hz_get_band_rows(ctx)
         m.hz_tuning_save(ctx, path, ins, outs)
         m.hz_tuning_save(ctx, path, ins, outs)  # replaces its own line
     with open(path) as f:
@@ -136,7 +137,9 @@ def test_tuning_record_roundtrip(tmp_path):
     with context(airlight_ema=0.9) as (m, ctx):
         m.hz_set_wave_bytes(ctx, 3 << 20)
         m.hz_set_video_path(ctx, not fused)
+        m.hz_set_band_rows(ctx, 45 if band != 45 else 60)
         assert m.hz_tuning_load(ctx, path, ins, outs)
         assert m.hz_get_wave_bytes(ctx) == best and m.hz_get_video_path(ctx) == fused
+        assert m.hz_get_band_rows(ctx) == band
         other = [to_dev(hazegen.make_frame(64, 48, seed=1))]
         assert not m.hz_tuning_load(ctx, path, other, [empty_dev(64, 48)[0]])

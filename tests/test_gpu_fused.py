@@ -102,3 +102,29 @@ def test_fused_maximum_dimensions():
         ref = O.dehaze_frame(I, oracle_params(patch=7))
         assert info.T == ref.T and info.cut_index == ref.cut_index
         assert u8_diff(o, ref.out)[0] <= 1
+
+
+@pytest.mark.parametrize("patch", [15, 7])
+def test_band_height_changes_no_byte(patch):
+    """Bands of the stencil kernel from one vHGW block to the whole frame
+    (and heights that are not a multiple of the patch side) give the same
+    bytes and selection, and the oracle's within 1 LSB."""
+    W, H = 481, 541
+    I = hazegen.make_frame(W, H, seed=17, beta=1.2)
+    ref = O.dehaze_frame(I, oracle_params(patch=patch))
+    with context(patch=patch) as (m, ctx):
+        It = to_dev(I, 3)
+        outs = []
+        for rows in (0, 1, 100, 1080, 16384):
+            m.hz_set_band_rows(ctx, rows)
+            bh = m.hz_get_band_rows(ctx)
+            assert bh % patch == 0 and bh >= max(rows, 1) and bh < max(rows, 270 if rows == 0 else rows) + patch
+            out, _ = empty_dev(W, H, 5, fill=11)
+            info = m.hz_dehaze_frame(ctx, It, out, want_info=True)
+            assert (info.T, info.cut_index) == (ref.T, ref.cut_index)
+            outs.append(out.cpu().numpy())
+        with pytest.raises(m.HzError):
+            m.hz_set_band_rows(ctx, 16385)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    assert u8_diff(outs[0], ref.out)[0] <= 1
