@@ -139,7 +139,24 @@ typedef struct hz_frame_info {
   float mean_luma;     /* mean BT.601 luminance of J (adaptive gamma; else 0) */
   float latency_ms;    /* hz_poll: time from hz_submit to the frame's completion
                           (outputs copied back); 0 for the other calls */
+  float ms_stage[6];   /* device milliseconds per stage of the launches that
+                          processed this frame, while profiling is on
+                          (hz_set_profiling; 0 otherwise), indexed by
+                          hz_stage_index. A launch covers many frames (a wave,
+                          a batch), so frames of one launch report the same
+                          time. Filled by hz_dehaze_frame, hz_dehaze_video,
+                          hz_dehaze_batch, hz_dehaze_image and hz_poll. */
 } hz_frame_info;
+
+/* Stages of hz_frame_info.ms_stage (Section V's order). */
+typedef enum hz_stage_index {
+  HZ_STAGE_INPUT = 0,         /* input preparation: resize to the processing size, NV12 conversion */
+  HZ_STAGE_DARK = 1,          /* dark channel (Eq. 2) or its block bounds */
+  HZ_STAGE_AIRLIGHT = 2,      /* top-K selection, A (Eq. 3) and its smoothing */
+  HZ_STAGE_TRANSMISSION = 3,  /* transmission plane and guided filter (Eq. 4-6; image mode) */
+  HZ_STAGE_RECOVER = 4,       /* transmission + Eq. 7-8, colour balance, quantisation */
+  HZ_STAGE_COPY = 5           /* hz_poll of a host-buffer frame: its batch's host copies (in + out) */
+} hz_stage_index;
 
 /* One frame of a mixed-size batch (hz_dehaze_batch). */
 typedef struct hz_frame_desc {

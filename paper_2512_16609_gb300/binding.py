@@ -61,6 +61,7 @@ class hz_frame_info(C.Structure):
         ("gamma", C.c_float),
         ("mean_luma", C.c_float),
         ("latency_ms", C.c_float),
+        ("ms_stage", C.c_float * 6),
     ]
 
     def as_dict(self):
@@ -69,6 +70,7 @@ class hz_frame_info(C.Structure):
             "cut_index": self.cut_index, "S": list(self.S), "T": self.T, "status": self.status,
             "gains": list(self.gains), "mean_jg": list(self.mean_jg),
             "gamma": self.gamma, "mean_luma": self.mean_luma, "latency_ms": self.latency_ms,
+            "ms_stage": list(self.ms_stage),
         }
 
 
@@ -100,6 +102,8 @@ class hz_server_stats(C.Structure):
 
 HZ_K_NAMES = ("dark", "select", "airlight", "recon", "balance", "trans", "guided", "resize")
 HZ_K_COUNT = 8
+# indexes of hz_frame_info.ms_stage
+HZ_STAGE_INPUT, HZ_STAGE_DARK, HZ_STAGE_AIRLIGHT, HZ_STAGE_TRANSMISSION, HZ_STAGE_RECOVER, HZ_STAGE_COPY = range(6)
 
 
 class hz_profile(C.Structure):

@@ -173,8 +173,49 @@ hz_status mark_done(hz_ctx* c, cudaStream_t s) {
   return HZ_OK;
 }
 
+void tag_frames(hz_ctx* c, const hz_frame_desc* fr, int n) {
+  std::lock_guard<std::mutex> lk(c->pmu);
+  if (!c->prof || c->tag_depth == 0) return;  // launches outside a tag scope keep no frames
+  c->tag_outs.resize(size_t(n));
+  for (int i = 0; i < n; ++i) c->tag_outs[size_t(i)] = fr[i].out;
+}
+
+static int stage_of(int kind) {
+  switch (kind) {
+    case HZ_K_RESIZE: return HZ_STAGE_INPUT;
+    case HZ_K_DARK: return HZ_STAGE_DARK;
+    case HZ_K_SELECT:
+    case HZ_K_AIRLIGHT: return HZ_STAGE_AIRLIGHT;
+    case HZ_K_TRANS:
+    case HZ_K_GUIDED: return HZ_STAGE_TRANSMISSION;
+    default: return HZ_STAGE_RECOVER;  // HZ_K_RECON, HZ_K_BALANCE
+  }
+}
+
+void stage_times(hz_ctx* c, uint64_t serial, hz_frame_info* infos, const void* const* outs, int n) {
+  if (!infos || n <= 0) return;
+  std::lock_guard<std::mutex> lk(c->pmu);
+  if (!c->prof) return;
+  for (const auto& p : c->pending) {
+    if (p.serial != serial || p.outs.empty()) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int st = stage_of(p.kind);
+    for (const void* o : p.outs)
+      for (int i = 0; i < n; ++i)
+        if (outs[i] == o) {
+          infos[i].ms_stage[st] += ms;
+          break;
+        }
+  }
+}
+
 void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video,
                uint8_t* base) {
+  tag_frames(c, fr, n);
   jobs.n = n;
   jobs.inject = int(c->inject);
   uint8_t* A = base ? base : c->arena.base;
@@ -245,6 +286,7 @@ cudaError_t copy_unaligned(const LaunchPlan& lp, const hz_frame_desc* fr, int n,
 // buffers (one launch for all of them), unaligned ones are copied.
 hz_status prepare_inputs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, uint8_t* base,
                          cudaStream_t s) {
+  tag_frames(c, fr, n);
   ResizeJobs rj, cj;  // resize (any format), NV12 conversion at the same size
   rj.n = cj.n = 0;
   rj.dbl = cj.dbl = 0;
@@ -835,8 +877,8 @@ static hz_status video_pipelined(hz_ctx* c, const hz_frame_desc* fr, const std::
 
 // Video frames on device memory: one wave runs on the caller's stream,
 // several go through the pipeline.
-static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
-                              HzStreamState* chain, HzFrameRec* rec_sink = nullptr) {
+static hz_status video_device_run(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
+                                  HzStreamState* chain, HzFrameRec* rec_sink) {
   std::vector<int> ws;
   split_waves(c, fr, n, ws);
   if (ws.size() > 2) return video_pipelined(c, fr, ws, s, infos, chain, rec_sink);
@@ -854,6 +896,23 @@ static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStr
   if (rec_sink)
     HZ_CK(c, cudaMemcpyAsync(rec_sink, c->arena.base, sizeof(HzFrameRec) * size_t(n), cudaMemcpyDeviceToHost, s));
   return read_infos(c, lp, n, s, infos, bal);
+}
+
+// The frames' outputs, the keys of their stage times.
+static std::vector<const void*> outs_of(const hz_frame_desc* fr, int n) {
+  std::vector<const void*> o(size_t(n > 0 ? n : 0));
+  for (int i = 0; i < n; ++i) o[size_t(i)] = fr[i].out;
+  return o;
+}
+
+// The infos (when given) are read after the frames completed; a call that
+// opens the tag scope adds the stage times.
+static hz_status video_device(hz_ctx* c, const hz_frame_desc* fr, int n, cudaStream_t s, hz_frame_info* infos,
+                              HzStreamState* chain, HzFrameRec* rec_sink = nullptr) {
+  TagScope ts(c);
+  HZ_TRY(video_device_run(c, fr, n, s, infos, chain, rec_sink));
+  if (ts.owner && infos) stage_times(c, ts.serial, infos, outs_of(fr, n).data(), n);
+  return HZ_OK;
 }
 
 // Signature of a device-buffer call for graph replay: the call's own bytes,
@@ -1022,7 +1081,9 @@ extern "C" hz_status hz_dehaze_batch(hz_ctx* c, const hz_frame_desc* frames, int
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   HZ_TRY(order_after_previous(c, s));
   if (infos) {
+    TagScope ts(c);
     HZ_TRY(run_batch(c, frames, n, s, infos, nullptr, nullptr));
+    if (ts.owner) stage_times(c, ts.serial, infos, outs_of(frames, n).data(), n);
   } else {
     const char tag[] = "batch";
     const std::string key = call_key(c, tag, sizeof tag, frames, sizeof(hz_frame_desc) * size_t(n));
@@ -1145,11 +1206,13 @@ extern "C" hz_status hz_dehaze_image(hz_ctx* c, const uint8_t* in, int32_t W, in
   hz_frame_desc d{in, in_pitch, out, out_pitch, W, H, -1, HZ_GUIDED};
   plan_frames(c->prm, &W, &H, 1, true, bal, lp, &d, true);
   HZ_TRY(arena_reserve(c, c->arena, lp.total, s));
+  TagScope ts(c);
   HZ_TRY(prepare_inputs(c, lp, &d, 1, c->arena.base, s));
   HzJobs jobs;
   fill_jobs(c, lp, &d, 1, jobs, TS_P);
   HZ_TRY(run_image_job(c, lp, jobs, bal, s));
   HZ_TRY(read_infos(c, lp, 1, s, info, bal));
+  if (ts.owner && info) stage_times(c, ts.serial, info, outs_of(&d, 1).data(), 1);
   return mark_done(c, s);
 }
 

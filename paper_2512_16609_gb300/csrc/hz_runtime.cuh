@@ -89,8 +89,18 @@ struct hz_ctx {
   uint64_t timed[HZ_K_COUNT] = {0};
   double prof_ms[HZ_K_COUNT] = {0};
   std::vector<cudaEvent_t> ev_pool;
-  struct PendingTime { int kind; cudaEvent_t a, b; };
+  // a timed launch: its class, events, and the frames it processed (their
+  // output pointers within the tag scope `serial`), for hz_frame_info.ms_stage
+  struct PendingTime {
+    int kind;
+    cudaEvent_t a, b;
+    uint64_t serial;
+    std::vector<const void*> outs;
+  };
   std::vector<PendingTime> pending;
+  uint64_t tag_serial = 0;            // current tag scope
+  int tag_depth = 0;                  // nesting of tag scopes (the outermost owns the serial)
+  std::vector<const void*> tag_outs;  // outputs of the frames being launched
 };
 
 namespace hz {
@@ -263,7 +273,7 @@ struct LaunchScope {
     cudaEvent_t b = take_event();
     if (!b) return;
     cudaEventRecord(b, s);
-    c->pending.push_back({kind, a, b});
+    c->pending.push_back({kind, a, b, c->tag_serial, c->tag_outs});
   }
   cudaEvent_t take_event() {
     if (!c->ev_pool.empty()) {
@@ -279,6 +289,34 @@ struct LaunchScope {
     return e;
   }
 };
+
+// A tag scope: the launches made while it is open are tagged with one serial
+// (scopes nest; the outermost one owns the serial and fills the stage times).
+struct TagScope {
+  hz_ctx* c;
+  bool owner;
+  uint64_t serial;
+  explicit TagScope(hz_ctx* c_) : c(c_) {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    owner = c->tag_depth++ == 0;
+    if (owner) {
+      ++c->tag_serial;
+      c->tag_outs.clear();
+    }
+    serial = c->tag_serial;
+  }
+  ~TagScope() {
+    std::lock_guard<std::mutex> lk(c->pmu);
+    --c->tag_depth;
+    if (c->tag_depth == 0) c->tag_outs.clear();
+  }
+};
+// The frames the next launches process (their output pointers).
+void tag_frames(hz_ctx* c, const hz_frame_desc* fr, int n);
+// Adds the device time of every timed launch of tag scope `serial` to the
+// ms_stage entry of each frame it processed (frame i: output outs[i]). The
+// launches must have completed. No-op while profiling is off.
+void stage_times(hz_ctx* c, uint64_t serial, hz_frame_info* infos, const void* const* outs, int n);
 
 hz_status arena_reserve(hz_ctx* c, Arena& a, size_t bytes, cudaStream_t s);
 // Copies of unaligned inputs into the plan's aligned buffers (scratch base).

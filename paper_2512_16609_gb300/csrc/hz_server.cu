@@ -44,6 +44,10 @@ struct Slot {
   // timed marks of the batch: its copies in start, its compute starts, its
   // copies out end (times against the server's reference event)
   cudaEvent_t t_in = nullptr, t_comp = nullptr, t_out = nullptr;
+  cudaEvent_t t_cend = nullptr;     // its compute ends
+  uint64_t serial = 0;              // tag scope of its launches (stage times)
+  std::vector<const void*> outs;    // the device outputs of its frames, by request
+  bool host_io = false;
   hz_status st = HZ_OK;
   bool busy = false;
 };
@@ -89,10 +93,11 @@ static void complete_loop(Server* S) {
     const double t = now_s();
     // device-side overlap: this batch's copies in (or its compute) began
     // before the previous batch's copies out had ended
-    float m_in = 0.f, m_comp = 0.f, m_out = 0.f;
+    float m_in = 0.f, m_comp = 0.f, m_out = 0.f, m_cend = 0.f;
     const bool timed = st == HZ_OK && cudaEventElapsedTime(&m_in, S->ev_ref, sl.t_in) == cudaSuccess &&
                        cudaEventElapsedTime(&m_comp, S->ev_ref, sl.t_comp) == cudaSuccess &&
-                       cudaEventElapsedTime(&m_out, S->ev_ref, sl.t_out) == cudaSuccess;
+                       cudaEventElapsedTime(&m_out, S->ev_ref, sl.t_out) == cudaSuccess &&
+                       cudaEventElapsedTime(&m_cend, S->ev_ref, sl.t_cend) == cudaSuccess;
     if (!timed) cudaGetLastError();
     const bool bal = c->prm.color_balance != 0;
     const int n = (int)sl.reqs.size();
@@ -105,6 +110,15 @@ static void complete_loop(Server* S) {
         plan_frames(c->prm, &r.W, &r.H, 1, false, false, lp, nullptr, true);
         recs_to_infos(sl.recs + k, lp, 1, &infos[i], bal);
       }
+      stage_times(c, sl.serial, infos.data(), sl.outs.data(), n);
+      bool prof;
+      {
+        std::lock_guard<std::mutex> lk(c->pmu);
+        prof = c->prof;
+      }
+      if (prof && timed && sl.host_io)
+        for (int i = 0; i < n; ++i)
+          if (sl.reqs[i].flags & HZ_IO_HOST) infos[i].ms_stage[HZ_STAGE_COPY] = (m_comp - m_in) + (m_out - m_cend);
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -191,13 +205,19 @@ static hz_status launch_batch(Server* S, Slot& sl) {
   HZ_CK(c, cudaEventRecord(sl.ev_h2d, S->s_h2d));
   HZ_CK(c, cudaStreamWaitEvent(S->s_comp, sl.ev_h2d, 0));
   HZ_CK(c, cudaEventRecord(sl.t_comp, S->s_comp));
+  sl.host_io = any_host;
+  sl.outs.resize(size_t(n));
+  for (int i = 0; i < n; ++i) sl.outs[size_t(i)] = fr[i].out;
   {
     std::lock_guard<std::mutex> lk(c->call_mu);
     cudaSetDevice(c->device);
     HZ_TRY(order_after_previous(c, S->s_comp));
+    TagScope ts(c);
+    sl.serial = ts.serial;
     HZ_TRY(run_batch(c, fr.data(), n, S->s_comp, nullptr, sl.recs, sl.order));
     HZ_TRY(mark_done(c, S->s_comp));
   }
+  HZ_CK(c, cudaEventRecord(sl.t_cend, S->s_comp));
   HZ_CK(c, cudaEventRecord(sl.ev_comp, S->s_comp));
   HZ_CK(c, cudaStreamWaitEvent(S->s_d2h, sl.ev_comp, 0));
   if (any_host) {
@@ -278,7 +298,7 @@ static hz_status server_start(hz_ctx* c) {
          cudaEventCreateWithFlags(&sl.ev_comp, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming | cudaEventBlockingSync) == cudaSuccess &&
          cudaEventCreate(&sl.t_in) == cudaSuccess && cudaEventCreate(&sl.t_comp) == cudaSuccess &&
-         cudaEventCreate(&sl.t_out) == cudaSuccess;
+         cudaEventCreate(&sl.t_out) == cudaSuccess && cudaEventCreate(&sl.t_cend) == cudaSuccess;
   }
   ok = ok && cudaEventCreate(&S->ev_ref) == cudaSuccess && cudaEventRecord(S->ev_ref, S->s_h2d) == cudaSuccess;
   if (!ok) {
@@ -315,6 +335,7 @@ void server_stop(hz_ctx* c) {
     if (sl.t_in) cudaEventDestroy(sl.t_in);
     if (sl.t_comp) cudaEventDestroy(sl.t_comp);
     if (sl.t_out) cudaEventDestroy(sl.t_out);
+    if (sl.t_cend) cudaEventDestroy(sl.t_cend);
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
   }
   if (S->ev_ref) cudaEventDestroy(S->ev_ref);
