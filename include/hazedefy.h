@@ -391,13 +391,15 @@ hz_status hz_autotune_wave_bytes(hz_ctx* ctx, const hz_frame_desc* frames, int32
 hz_status hz_set_graph_replay(hz_ctx* ctx, int on);
 
 /* Failure detection test hook (no counterpart in the paper). Every wait a
- * kernel makes on the device (the dark-channel kernel's wait for its staged
- * input rows) gives up after one second: the frame's hz_frame_info.status
+ * kernel makes on the device (the waits for staged input rows of the
+ * patch-minimum path's dark-channel kernel and of the fused path's
+ * transmission and reconstruction kernel) gives up after one second: the
+ * frame's hz_frame_info.status
  * becomes HZ_EDEVICE_TIMEOUT, a call that returns frame infos returns
  * HZ_EDEVICE_TIMEOUT (without infos the status is not read), that frame's
  * output is undefined, and the context stays usable. While mask holds
- * HZ_INJECT_WITHHOLD_ROW_COPIES the dark-channel kernel withholds the input
- * copies of the first row chunk of every region, so that wait runs out:
+ * HZ_INJECT_WITHHOLD_ROW_COPIES those kernels withhold the input copies of
+ * the first row chunk of every region or tile, so that wait runs out:
  * each affected launch takes about two seconds and no GPU fault is
  * involved. mask = 0 (the default) restores normal operation; other bits
  * are HZ_EINVAL. */

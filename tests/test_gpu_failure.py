@@ -1,8 +1,10 @@
 """Failure detection on the GPU without a fault. With the host-set injection
-flag on, the dark-channel kernel withholds the input copies of one row chunk
-per region, so its bounded wait (one second of the global timer) runs out:
-the frame reports HZ_EDEVICE_TIMEOUT, the call returns it, and the same
-context then dehazes the following calls as the oracle does."""
+flag on, the kernel that stages input rows with bulk copies (the dark-channel
+kernel of the patch-minimum path, the transmission and reconstruction kernel
+of the fused path) withholds the copies of its first row chunk, so its
+bounded wait (one second of the global timer) runs out: the frame reports
+HZ_EDEVICE_TIMEOUT, the call returns it, and the same context then dehazes
+the following calls as the oracle does."""
 import ctypes as C
 import time
 
@@ -16,11 +18,13 @@ from tests.gpu_util import context, empty_dev, oracle_params, to_dev, torch, u8_
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_device_wait_reports_timeout_and_context_recovers():
-    W, H = 640, 90  # two strips x two bands: four regions, all resident at once
+@pytest.mark.parametrize("fused", [True, False])
+def test_bounded_device_wait_reports_timeout_and_context_recovers(fused):
+    W, H = 640, 90  # a few regions or tiles, all resident at once
     I = hazegen.make_frame(W, H, seed=11, beta=1.0)
     ref = O.dehaze_frame(I, oracle_params())
     with context() as (m, ctx):
+        m.hz_set_video_path(ctx, fused)
         src = to_dev(I)
         out, _ = empty_dev(W, H)
         pi, _, _, ip = m.binding.frame_args(src)
