@@ -832,6 +832,30 @@ __device__ __forceinline__ void v2_item(const HzJob& jb, const HzKParams& kp, co
   }
 }
 
+// One output pixel j of an item per lane: the same operations, in the same
+// order and rounding, as v2_item's for that pixel (the window minimum is
+// exact in any order). Used for the few items left after the whole warps of
+// a row block, so that a warp is not spent on one item in one lane.
+template <int R, bool G1>
+__device__ __forceinline__ void v2_out_pixel(const HzJob& jb, const HzKParams& kp, const P3Const& K,
+                                             const float* vr, const unsigned char* ir, int Y, int x_out, int j) {
+  using G = V2S<R>;
+  float m = vr[G::OFFV + j];
+#pragma unroll
+  for (int i = 1; i < G::P; ++i) m = fminf(m, vr[G::OFFV + j + i]);
+  const float t = fmaxf(fmaf(-kp.omega, m, 1.f), kp.t0);
+  const float r = rcpa(t);
+  uint8_t* Op = jb.out + (long long)Y * jb.out_pitch + 3LL * (x_out + j);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float In = fmaf(__uint_as_float(0x4B000000u | ir[3 * j + c]), INV255, -TWO23 * INV255);
+    const float d = In + (-K.A[c]);
+    float J = __saturatef(fmaf(d, r, K.A[c]));
+    if (!G1) J = ex2a(lg2a(J) * K.gamma_inv);
+    Op[c] = uint8_t(__float_as_uint(fmaf(J, 255.f, MAGIC_RINT)) & 0xffu);
+  }
+}
+
 template <int R>
 __global__ void __launch_bounds__(V2_NT, V2S<R>::MINB) k_v2(const __grid_constant__ HzJobs jobs, const HzKParams kp) {
   using G = V2S<R>;
@@ -919,8 +943,12 @@ __global__ void __launch_bounds__(V2_NT, V2S<R>::MINB) k_v2(const __grid_constan
     if (tid >= V2_CT) {
       if (k + 1 <= kmax) v2_issue<R>(jb, k + 1, ya, xs, xa, xb, smem, mbar, tid - V2_CT, 0);
     } else if (k >= 1) {
-      // output rows y0 + P (k - 1) + a: items (segment, row), rows fastest
-      for (int it = tid; it < P * G::NSEG; it += V2_CT) {
+      // output rows y0 + P (k - 1) + a: items (segment, row), rows fastest;
+      // one item per thread in whole warps, the last NIT % 32 items (when
+      // few) sixteen lanes each in the warp with the fewest items
+      constexpr int NIT = P * G::NSEG, LEFT = NIT % 32;
+      constexpr int FULL = (NIT > 32 && LEFT <= 14) ? NIT - LEFT : NIT;
+      for (int it = tid; it < FULL; it += V2_CT) {
         const int seg = it / P, a = it - seg * P;
         const int Y = y0 + P * (k - 1) + a;
         const int x_out = x0 + 16 * seg;
@@ -930,6 +958,23 @@ __global__ void __launch_bounds__(V2_NT, V2S<R>::MINB) k_v2(const __grid_constan
         const float* vr = Vk + a * V2_VST + G::OFFQ + 16 * seg;
         if (kp.gamma_is_one) v2_item<R, true>(jb, kp, K, vr, ir, Y, x_out, min(16, W - x_out));
         else v2_item<R, false>(jb, kp, K, vr, ir, Y, x_out, min(16, W - x_out));
+      }
+      if constexpr (FULL < NIT) {
+        constexpr int LW = (FULL % V2_CT == 0) ? V2_CT / 32 - 1 : (FULL % V2_CT) / 32;
+        if ((tid >> 5) == LW) {
+          const int lane = tid & 31;
+          for (int it = FULL + (lane >> 4); it < NIT; it += 2) {
+            const int seg = it / P, a = it - seg * P;
+            const int Y = y0 + P * (k - 1) + a;
+            const int x_out = x0 + 16 * seg, j = lane & 15;
+            if (Y >= y0 + rows_out || x_out + j >= W) continue;
+            const int rr = P * (k - 1) + a + R;
+            const unsigned char* ir = smem + (((rr / P) % 3) * P + rr % P) * V2_SLOT + G::S0 + 3 * (G::RA + 16 * seg);
+            const float* vr = Vk + a * V2_VST + G::OFFQ + 16 * seg;
+            if (kp.gamma_is_one) v2_out_pixel<R, true>(jb, kp, K, vr, ir, Y, x_out, j);
+            else v2_out_pixel<R, false>(jb, kp, K, vr, ir, Y, x_out, j);
+          }
+        }
       }
     }
   }

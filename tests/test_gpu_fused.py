@@ -31,7 +31,9 @@ def _both_paths(m, ctx, It, W, H):
     (241, 271, 15, 0.001, 1, "haze"), (481, 541, 15, 0.01, 16, "haze"), (33, 9, 31, 0.2, 0, "noise"),
     (300, 200, 1, 0.001, 0, "haze"), (300, 200, 3, 0.02, 5, "haze"), (257, 129, 7, 0.3, 0, "noise"),
     (500, 120, 19, 0.001, 0, "haze"), (1023, 37, 29, 0.001, 2, "haze"), (64, 64, 15, 1.0, 0, "haze"),
-    (200, 150, 15, 0.001, 0, "const"), (200, 150, 9, 0.9, 0, "levels")])
+    (200, 150, 15, 0.001, 0, "const"), (200, 150, 9, 0.9, 0, "levels"),
+    (331, 97, 5, 0.01, 0, "haze"), (263, 301, 11, 0.002, 4, "haze"), (517, 205, 21, 0.001, 0, "haze"),
+    (300, 260, 23, 0.005, 0, "haze"), (260, 140, 13, 0.001, 0, "haze")])
 def test_fused_path_matches_oracle_and_patch_minimum_path(W, H, patch, frac, pad, kind):
     if kind == "haze":
         I = hazegen.make_frame(W, H, seed=W + H + patch, beta=1.1)
