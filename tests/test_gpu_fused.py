@@ -130,3 +130,24 @@ def test_band_height_changes_no_byte(patch):
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
     assert u8_diff(outs[0], ref.out)[0] <= 1
+
+
+def test_selection_rescans_levels_below_its_list():
+    """Bright stripes three block rows tall every eight block rows: 15,360
+    blocks share the top bound levels, more than a selection rank's list
+    takes, so the ranks list only the highest levels and reach the rest by
+    rescans of the block plane. Selection and bytes as the oracle and the
+    patch-minimum path."""
+    W, H = 4096, 640
+    rng = np.random.default_rng(5)
+    I = np.full((H, W, 3), 10, np.uint8)
+    rows = ((np.arange(H) // 8) % 8) < 3
+    I[rows] = (240 + rng.integers(0, 16, size=(int(rows.sum()), W, 3))).astype(np.uint8)
+    with context() as (m, ctx):
+        (of, op), (inf_f, inf_p) = _both_paths(m, ctx, to_dev(I), W, H)
+    ref = O.dehaze_frame(I, oracle_params())
+    for info in (inf_f, inf_p):
+        assert (info.T, info.n_above, info.cut_index) == (ref.T, ref.n_above, ref.cut_index)
+        assert list(info.S) == [int(v) for v in ref.S]
+    np.testing.assert_array_equal(of, op)
+    assert u8_diff(of, ref.out)[0] <= 1
