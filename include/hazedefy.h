@@ -359,7 +359,7 @@ hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
 
 /* Autotuner (no counterpart in the paper): runs the given batch (layout and
  * rules as for hz_dehaze_batch, which it calls) at each candidate wave
- * size, 8, 16, 32, 64, 128, 192, 256, 384 and 512 MiB (a launch takes at
+ * size, 8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 416, 448 and 512 MiB (a launch takes at
  * most 64 frames whatever the size), on each video path that the
  * parameters allow (fused and patch-minimum, see hz_set_video_path), two
  * untimed and three timed runs each (CUDA events on cuda_stream), and keeps
@@ -369,7 +369,7 @@ hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
  * the fastest. Every run starts from the stream states at
  * entry, which are restored at the end, so the outputs equal those of one
  * hz_dehaze_batch call and the states are left unchanged. *best_bytes (optional) receives the chosen size; ms_per_candidate
- * (optional, n_candidates >= 9 entries) the mean milliseconds per batch of
+ * (optional, n_candidates >= 13 entries) the mean milliseconds per batch of
  * each candidate. Synchronises the stream. Errors: HZ_EINVAL for a bad frame
  * list or a short ms_per_candidate, HZ_ECUDA / HZ_ENOMEM from the runs (the
  * previous wave size and path are kept). ms_per_candidate holds the chosen

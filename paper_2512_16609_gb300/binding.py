@@ -474,7 +474,7 @@ def hz_set_wave_bytes(ctx, nbytes: int):
     return _check(lib().hz_set_wave_bytes(ctx, int(nbytes)), ctx, "hz_set_wave_bytes")
 
 
-TUNE_WAVE_MIB = (8, 16, 32, 64, 128, 192, 256, 384, 512)
+TUNE_WAVE_MIB = (8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 416, 448, 512)
 
 
 def _descs(frames, outs, stream_ids=None, guided=None, nv12=None):

@@ -1416,7 +1416,7 @@ extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
 // the fastest. Every run starts from the stream states saved at entry, which
 // are restored at the end: the tuning leaves no trace beyond the outputs,
 // which equal those of one ordinary call.
-static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256, 384, 512};
+static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 416, 448, 512};
 // band heights of the fused stencil kernel (rows; a multiple of the patch side is taken)
 static const int TUNE_BAND_ROWS[] = {90, 135, 270, 540, 1080};
 
@@ -1467,9 +1467,14 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
     if (st == HZ_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(c, HZ_ECUDA, "event record failed");
     for (int r = 0; r < 3 && st == HZ_OK; ++r) st = one_run();
     float ms = 0.f;
-    if (st == HZ_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-      st = fail(c, HZ_ECUDA, "event timing failed");
+    if (st == HZ_OK) {
+      cudaError_t e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess)
+        st = fail(c, HZ_ECUDA, "timing of path %d at %zu MiB waves failed: %s", c->fused ? 1 : 0,
+                  c->wave_bytes >> 20, cudaGetErrorString(e));
+    }
     if (st != HZ_OK) break;
     ms /= 3.f;
     ms_path[path][k] = ms;
@@ -1491,9 +1496,13 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
       if (st == HZ_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(c, HZ_ECUDA, "event record failed");
       for (int r = 0; r < 3 && st == HZ_OK; ++r) st = one_run();
       float ms = 0.f;
-      if (st == HZ_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        st = fail(c, HZ_ECUDA, "event timing failed");
+      if (st == HZ_OK) {
+        cudaError_t e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess)
+          st = fail(c, HZ_ECUDA, "timing of %d-row bands failed: %s", c->v2_band, cudaGetErrorString(e));
+      }
       if (st != HZ_OK) break;
       ms /= 3.f;
       if (ms < best_ms) {

@@ -447,9 +447,11 @@ __device__ __forceinline__ void sel_for_blocks(const HzJob& jb, int rank, int lo
 // One frame's selection on a cluster of SEL_CL blocks: every rank lists
 // and evaluates the candidate blocks of its rows of the block plane; the
 // exact histogram and the ties' span live in the leader's (rank 0) shared
-// memory, which the ranks update with distributed-shared-memory atomics; a
-// cluster barrier closes every level round, so all ranks read the same
-// counts and take the same levels. The leader then makes the cut.
+// memory, which the ranks update with distributed-shared-memory atomics. A
+// level round reads the counts, meets at a cluster barrier, adds its counts
+// and meets again, so no rank adds counts while another still reads them:
+// all ranks read the same counts, take the same levels and pass the same
+// barriers. The leader then makes the cut.
 template <int LS>
 __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
     k_sel(const __grid_constant__ HzJobs jobs, const HzKParams kp, int R) {
@@ -527,6 +529,9 @@ __global__ void __cluster_dims__(SEL_CL, 1, 1) __launch_bounds__(SEL_THREADS, 4)
     if (tid < hi && (unsigned long long)sX[tid] + sB[tid] - sB[hi] >= K) atomicMax(&s_lo, tid);
     __syncthreads();
     const int lo = s_lo;
+    // every rank has read the counts (here and for the previous round's T)
+    // before any rank adds this round's: all ranks take the same levels
+    cl.sync();
     sel_for_blocks(jb, rank, lo, hi, L0, nlist, list, lvl, cand, &s_nc,
                    [&](int b) { sel_block_exact<LS>(jb, R, b, hd, reg, vmb[warp]); });
     // the round's counts into the cluster histogram, one atomic per level

@@ -110,7 +110,7 @@ def test_autotune_keeps_outputs_and_states():
         best, table = m.hz_autotune_wave_bytes(ctx, ins, outs, stream_ids=sids)
         assert best in [mb << 20 for mb in m.TUNE_WAVE_MIB]
         assert m.hz_get_wave_bytes(ctx) == best
-        assert all(v > 0 for v in table.values()) and len(table) == len(m.TUNE_WAVE_MIB) == 9
+        assert all(v > 0 for v in table.values()) and len(table) == len(m.TUNE_WAVE_MIB) == 13
         assert [m.hz_stream_get_state(ctx, sid) for sid in sids] == before
         # every tuning run started from the same states as this plain second call
         m.hz_dehaze_batch(ctx, ins, ref, stream_ids=sids)
