@@ -364,7 +364,7 @@ hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
  * parameters allow (fused and patch-minimum, see hz_set_video_path), two
  * untimed and three timed runs each (CUDA events on cuda_stream), and keeps
  * the fastest wave size and path as the context's; when the fused path wins
- * it then times band heights of 90, 135, 270, 540 and 1080 rows for that
+ * it then times band heights of 90, 135, 180, 270, 360, 540 and 1080 rows for that
  * path's stencil kernel (hz_set_band_rows) at the chosen wave size and keeps
  * the fastest. Every run starts from the stream states at
  * entry, which are restored at the end, so the outputs equal those of one

@@ -1418,7 +1418,7 @@ extern "C" hz_status hz_get_wave_bytes(const hz_ctx* c, size_t* bytes) {
 // which equal those of one ordinary call.
 static const size_t TUNE_WAVE_MIB[] = {8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 416, 448, 512};
 // band heights of the fused stencil kernel (rows; a multiple of the patch side is taken)
-static const int TUNE_BAND_ROWS[] = {90, 135, 270, 540, 1080};
+static const int TUNE_BAND_ROWS[] = {90, 135, 180, 270, 360, 540, 1080};
 
 extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* frames, int32_t n, void* cuda_stream,
                                             size_t* best_bytes, float* ms_per_candidate, int32_t n_candidates) {

@@ -151,3 +151,23 @@ def test_selection_rescans_levels_below_its_list():
         assert list(info.S) == [int(v) for v in ref.S]
     np.testing.assert_array_equal(of, op)
     assert u8_diff(of, ref.out)[0] <= 1
+
+
+def test_fused_pipeline_repeats_bytes_under_load():
+    """Many small waves of a 720p sequence through the three-stream pipeline
+    (selections of several waves run beside the other kernels): repeated
+    calls give the same bytes and airlight chain, and the patch-minimum path
+    the same bytes."""
+    W, H, F = 1280, 720, 48
+    seq = torch.from_numpy(hazegen.make_sequence(W, H, F, seed=31, period=F)).cuda()
+    with context(airlight_ema=0.9) as (m, ctx):
+        m.hz_set_wave_bytes(ctx, 4 * 3 * W * H)  # four frames per wave: twelve waves
+        res = []
+        for fused in (True, True, True, False):
+            m.hz_set_video_path(ctx, fused)
+            out = torch.empty_like(seq)
+            infos = m.hz_dehaze_video(ctx, seq, out, want_info=True)
+            res.append((out.cpu().numpy(), [(i.T, i.cut_index, tuple(i.A)) for i in infos]))
+    for o, inf in res[1:]:
+        np.testing.assert_array_equal(o, res[0][0])
+        assert inf == res[0][1]
