@@ -28,7 +28,7 @@ __host__ __device__ constexpr int p1_band_blocks(int R) {
 __host__ __device__ constexpr int p1_band_rows(int R) { return p1_band_blocks(R) * (2 * R + 1); }
 // ---- selection: blocks per frame (each loops over every P2_BLOCKS-th
 // region; only regions whose maximum reaches the threshold are scanned) ---
-constexpr int P2_BLOCKS = 16;
+constexpr int P2_BLOCKS = 64;
 __host__ __device__ constexpr int p2_blocks(int nitems) { return nitems < P2_BLOCKS ? nitems : P2_BLOCKS; }
 // ---- pointwise reconstruction kernels ----------------------------------
 constexpr int P3_THREADS = 256;
