@@ -407,20 +407,26 @@ __device__ __forceinline__ void sel_scan_plane(const HzJob& jb, int rank, Fn&& f
 
 // This rank's blocks with lo <= B < hi, one warp each (fn(block)): from the
 // list where it covers the levels (every block of the rank with B >= L0 is
-// listed), the rest by chunked rescans of the block plane.
+// listed), the rest by chunked rescans of the block plane. Either way the
+// blocks to take are first gathered in cand and then dealt to the warps in
+// turn, so that a cluster of candidates in the frame (a bright region lists
+// its blocks side by side) does not fall on one warp. What fn does for a
+// block does not depend on the order.
 template <class Fn>
 __device__ __forceinline__ void sel_for_blocks(const HzJob& jb, int rank, int lo, int hi, int L0, int nlist,
                                                const int* list, const uint8_t* lvl, int* cand, int* s_nc, Fn&& fn) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e0 = 32 * warp; e0 < nlist; e0 += 32 * SEL_WARPS) {
-    const int e = e0 + lane;
-    const bool take = e < nlist && lvl[e] >= lo && lvl[e] < hi;
-    unsigned mask = __ballot_sync(0xffffffffu, take);
-    while (mask) {
-      const int l = __ffs(mask) - 1;
-      mask &= mask - 1;
-      fn(list[e0 + l]);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int l0 = 0; l0 < nlist; l0 += SEL_CHUNK) {
+    __syncthreads();
+    if (tid == 0) *s_nc = 0;
+    __syncthreads();
+    for (int i = tid; i < SEL_CHUNK && l0 + i < nlist; i += SEL_THREADS) {
+      const int e = l0 + i;
+      if (lvl[e] >= lo && lvl[e] < hi) cand[atomicAdd(s_nc, 1)] = list[e];
     }
+    __syncthreads();
+    const int nc = *s_nc;
+    for (int c = warp; c < nc; c += SEL_WARPS) fn(cand[c]);
   }
   if (lo < L0) {
     // rescan of the levels below the list, SEL_CHUNK blocks per pass
