@@ -362,7 +362,9 @@ hz_status hz_get_wave_bytes(const hz_ctx* ctx, size_t* bytes);
  * size, 8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 416, 448 and 512 MiB (a launch takes at
  * most 64 frames whatever the size), on each video path that the
  * parameters allow (fused and patch-minimum, see hz_set_video_path), two
- * untimed and three timed runs each (CUDA events on cuda_stream), and keeps
+ * untimed and three timed runs each (CUDA events on cuda_stream; run as
+ * hz_dehaze_batch runs them, through graph replay when hz_set_graph_replay
+ * has turned it on), and keeps
  * the fastest wave size and path as the context's; when the fused path wins
  * it then times band heights of 90, 135, 180, 270, 360, 540 and 1080 rows for that
  * path's stencil kernel (hz_set_band_rows) at the chosen wave size and keeps

@@ -1453,11 +1453,15 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
       cudaMemcpyAsync(saved, c->states, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     st = fail(c, HZ_ECUDA, "autotune setup failed");
-  // every run starts from the saved states (a 48-byte-per-stream copy)
+  // every run starts from the saved states (a 48-byte-per-stream copy) and
+  // runs as hz_dehaze_batch would: through graph replay when it is on
   auto one_run = [&]() -> hz_status {
     if (cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return fail(c, HZ_ECUDA, "restoring stream states failed");
-    return run_batch(c, frames, n, s, nullptr, nullptr, nullptr);
+    if (!c->graphs) return run_batch(c, frames, n, s, nullptr, nullptr, nullptr);
+    const char tag[] = "batch";
+    const std::string key = call_key(c, tag, sizeof tag, frames, sizeof(hz_frame_desc) * size_t(n));
+    return graph_call(c, s, key, [&](cudaStream_t st) { return run_batch(c, frames, n, st, nullptr, nullptr, nullptr); });
   };
   for (int pk = 0; pk < npath * NCAND && st == HZ_OK; ++pk) {
     const int k = pk % NCAND, path = pk / NCAND;

@@ -99,8 +99,10 @@ def test_graph_replay_repeats_and_recaptures():
         m.hz_set_graph_replay(ctx, False)
 
 
-def test_autotune_keeps_outputs_and_states():
+@pytest.mark.parametrize("graphs", [False, True])
+def test_autotune_keeps_outputs_and_states(graphs):
     with context(airlight_ema=0.9) as (m, ctx):
+        m.hz_set_graph_replay(ctx, graphs)  # the tuner times its runs as the calls would run
         ins = _batch_inputs()
         outs = [empty_dev(W, H, 1)[0] for (W, H, _) in SPECS]
         ref = [empty_dev(W, H, 1)[0] for (W, H, _) in SPECS]
