@@ -237,14 +237,17 @@ __device__ __forceinline__ void sel_block_sums(const HzJob& jb, int T, int b, un
   if (lane < 4 * S) racc[lane] = 0u;
   __syncwarp();
   bool tie = false;
+  // the pixel's D and its bytes are loaded together (one memory latency per
+  // block rather than two)
+#pragma unroll
   for (int idx = lane; idx < S * S; idx += 32) {
     const int r = idx / S, j = idx - r * S;
     const int yy = Y0 + r, xx = X0 + j;
     if (yy >= jb.H || xx >= jb.W) continue;
     const int d = __ldcg(jb.dx + (long long)yy * jb.dx_pitch + xx);
-    if (d < T) continue;
     const uint8_t* q = jb.in + (long long)yy * jb.in_pitch + 3LL * xx;
     const unsigned r8 = __ldg(q), g8 = __ldg(q + 1), b8 = __ldg(q + 2);
+    if (d < T) continue;
     if (d > T) {
       ar += r8; ag += g8; ab += b8;
     } else {
