@@ -436,9 +436,13 @@ hz_status hz_get_video_path(const hz_ctx* ctx, int* fused);
  * `patch` rows (the vertical minimum is taken in blocks of the window's
  * height). Taller bands re-read fewer halo rows (2 x (patch / 2) per band)
  * but give fewer blocks per launch. rows = 0 restores the default (270);
- * 1..16384 are accepted, others HZ_EINVAL. hz_get_band_rows returns the
- * height in use (after rounding). Results do not depend on it. The
- * autotuner sets it (see hz_autotune_wave_bytes). */
+ * 1..16384 are accepted, others HZ_EINVAL. A height set here is used as
+ * given in every launch; the default and the autotuner's choice (see
+ * hz_autotune_wave_bytes, hz_tuning_load) are lowered, to no less than three
+ * blocks of `patch` rows, for a launch with fewer tiles than the GPU holds
+ * at once (three per SM), so that a launch of a few frames still fills the
+ * GPU. hz_get_band_rows returns the context's height (after rounding).
+ * Results do not depend on it. */
 hz_status hz_set_band_rows(hz_ctx* ctx, int32_t rows);
 hz_status hz_get_band_rows(const hz_ctx* ctx, int32_t* rows);
 /* Graphs captured and replays done since the context was created. */

@@ -213,9 +213,34 @@ void stage_times(hz_ctx* c, uint64_t serial, hz_frame_info* infos, const void* c
   }
 }
 
+// Band height of the fused stencil kernel for a launch over these frames:
+// the context's (as given when the caller set it), else lowered (to no less
+// than three blocks of P rows) while the launch has fewer tiles than the GPU
+// holds at once, so that a launch of a few frames still fills the SMs.
+static int launch_band_rows(const hz_ctx* c, const LaunchPlan& lp, int n) {
+  const int R = c->prm.patch / 2, P = 2 * R + 1;
+  int bh = v2_band_rows(R, c->v2_band);
+  if (c->v2_band_exact) return bh;
+  const int floor_rows = 3 * P;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const long long want = 3LL * sms;  // resident k_v2 blocks: three per SM
+  for (;;) {
+    long long tiles = 0;
+    for (int i = 0; i < n; ++i)
+      tiles += (long long)v2_tiles_x(R, lp.fp[i].W) * v2_tiles_y(R, lp.fp[i].H, bh);
+    if (tiles >= want || bh <= floor_rows) return bh;
+    bh = std::max(floor_rows, v2_band_rows(R, bh / 2));
+  }
+}
+
 void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, HzJobs& jobs, int tsrc_video,
                uint8_t* base) {
   tag_frames(c, fr, n);
+  const int v2_bh = launch_band_rows(c, lp, n);
   jobs.n = n;
   jobs.inject = int(c->inject);
   uint8_t* A = base ? base : c->arena.base;
@@ -255,8 +280,8 @@ void fill_jobs(hz_ctx* c, const LaunchPlan& lp, const hz_frame_desc* fr, int n, 
     j.bnd_w = f.bnd_w;
     j.bnd_h = f.bnd_h;
     j.v2_tx = v2_tiles_x(c->prm.patch / 2, f.W);
-    j.v2_bh = v2_band_rows(c->prm.patch / 2, c->v2_band);
-    j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H, c->v2_band);
+    j.v2_bh = v2_bh;
+    j.v2_ty = v2_tiles_y(c->prm.patch / 2, f.H, v2_bh);
     j.dx = A + f.off_P;  // the P region holds the candidates' exact D in the fused path
     j.dx_pitch = f.P_pitch;
     j.b1_xc = (((j.W + B1_PX - 1) / B1_PX) + B1_THREADS - 1) / B1_THREADS;
@@ -1490,9 +1515,11 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
   }
   // the stencil kernel's band height, on the fused path at the chosen wave size
   int best_band = keep_band;
+  const bool keep_exact = c->v2_band_exact;
   if (st == HZ_OK && best_fused && npath == 2) {
     c->fused = true;
     c->wave_bytes = best;
+    c->v2_band_exact = false;  // the tuner's heights are lowered for small launches
     for (int k = 0; k < int(sizeof TUNE_BAND_ROWS / sizeof TUNE_BAND_ROWS[0]) && st == HZ_OK; ++k) {
       c->v2_band = TUNE_BAND_ROWS[k];
       if (c->v2_band == keep_band) continue;  // timed in the sweep above
@@ -1516,6 +1543,7 @@ extern "C" hz_status hz_autotune_wave_bytes(hz_ctx* c, const hz_frame_desc* fram
     }
   }
   c->v2_band = (st == HZ_OK) ? best_band : keep_band;
+  if (st != HZ_OK) c->v2_band_exact = keep_exact;
   if (ms_per_candidate && st == HZ_OK)
     for (int k = 0; k < NCAND; ++k) ms_per_candidate[k] = ms_path[(npath == 2 && !best_fused) ? 1 : 0][k];
   if (saved && cudaMemcpyAsync(c->states, saved, sbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess && st == HZ_OK)
@@ -1619,6 +1647,7 @@ extern "C" hz_status hz_tuning_load(hz_ctx* c, const char* file, const hz_frame_
   c->fused = path == 1;
   c->wave_bytes = size_t(wave);
   c->v2_band = band;
+  c->v2_band_exact = false;
   if (found) *found = 1;
   return HZ_OK;
 }
@@ -1653,6 +1682,7 @@ extern "C" hz_status hz_set_band_rows(hz_ctx* c, int32_t rows) {
   if (rows < 0 || rows > V2_BAND_MAX) return fail(c, HZ_EINVAL, "band rows must be in 0..%d", V2_BAND_MAX);
   std::lock_guard<std::mutex> lk(c->call_mu);
   c->v2_band = rows ? rows : V2_BAND;
+  c->v2_band_exact = rows != 0;
   return HZ_OK;
 }
 

@@ -46,6 +46,7 @@ struct hz_ctx {
   hz::HzFrameRec* rec_host = nullptr;   // pinned, MAXJ records
   bool fused = true;                    // fused video kernels where the parameters allow them
   int v2_band = 270;                    // requested output rows per band of the fused stencil kernel
+  bool v2_band_exact = false;           // set by hz_set_band_rows: used as given in every launch
   cudaEvent_t done_ev = nullptr;        // end of the last call's work
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[hz::HOSTIO_BUFS] = {}, ev_comp[hz::HOSTIO_BUFS] = {}, ev_out[hz::HOSTIO_BUFS] = {};
